@@ -1,0 +1,57 @@
+"""Planted mistakes in the oracle must trip at least one pin (CPU only).
+
+Each case swaps one ingredient of the oracle for a plausible wrong one and
+checks that the corresponding pin predicate rejects it.
+"""
+import numpy as np
+
+import oracle
+from tests import goldens
+
+RNG = np.random.default_rng(77)
+
+
+def _power_form_ok(W):
+    E = goldens.power_form()
+    k = np.array([2, 5, 9])
+    return sorted(tuple(e @ k) for e in E) == sorted(tuple(w @ k) for w in W)
+
+
+def test_transposed_group_action_is_caught(monkeypatch):
+    assert _power_form_ok(oracle.weyl_group())
+    Wt = np.transpose(oracle.weyl_group(), (0, 2, 1)).copy()
+    assert not _power_form_ok(Wt)
+    # and the exchanged-sum form built on it leaves the dense definition
+    monkeypatch.setattr(oracle, "weyl_group", lambda: Wt)
+    n = 3
+    x = RNG.standard_normal((n, n, n))
+    monkeypatch.undo()
+    ref = oracle.forward_dense(x, n)
+    monkeypatch.setattr(oracle, "weyl_group", lambda: Wt)
+    bad = oracle.forward_sum_fft(x, n)
+    assert np.abs(bad - ref).max() > 1e-3
+
+
+def test_wrong_skew_is_caught():
+    n = 4
+    good = oracle.sample_points(n)
+    e = np.array([n, 0, 0])
+    assert max(abs(oracle.chebyshev(e, t)) for t in good) < 1e-13
+    # a dropped offset and a mistyped one (3/8 -> 1/8)
+    for skew in (((0, 0, 0), 8), ((1, 0, 1), 8)):
+        bad = oracle.sample_points(n, skew=skew)
+        assert max(abs(oracle.chebyshev(e, t)) for t in bad) > 1e-3
+
+
+def test_wrong_dft_sign_is_caught(monkeypatch):
+    n = 4
+    x = RNG.standard_normal((n, n, n)) + 1j * RNG.standard_normal((n, n, n))
+    ref = oracle.forward_dense(x, n)
+    monkeypatch.setattr(oracle.np.fft, "ifftn", lambda a, axes=None: np.fft.fftn(a, axes=axes) / n ** 3)
+    assert np.abs(oracle.forward_sum_fft(x, n) - ref).max() > 1e-3
+
+
+def test_dropped_normalisation_is_caught():
+    th = RNG.random(3)
+    t0 = oracle.chebyshev((0, 0, 0), th)
+    assert abs(t0 - 1) < 1e-15 and abs(24 * t0 - 1) > 1
