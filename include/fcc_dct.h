@@ -1,0 +1,163 @@
+/*
+ * fcc_dct.h -- C ABI of libfccdct, a CUDA (sm_103a) implementation of the FCC
+ * cosine transform DCT_{n x n x n} of Seifert, Hueper and Uhl, "Fast cosine
+ * transform for FCC lattices" (2018).
+ *
+ * The operation (Def. 2 and its explicit matrix form, Sec. 4.A):
+ *
+ *   y[i,l,q] = sum_{0 <= j,k,p < n} x[j,k,p] * T_{j,k,p}(theta_{i,l,q}),
+ *   theta_{i,l,q} = ((1/8 + i)/n, l/n, (3/8 + q)/n)          (Lemma 1),
+ *   T_k(theta)    = (1/24) sum_{w in W} exp(2 pi i (w k).theta)
+ *                   (Def. 1 with the power form of Sec. 3; W is the group
+ *                   of order 24 generated by the printed s1, s2, s3, acting
+ *                   on k from the left).
+ *
+ * "forward" is y = D x (coefficients of the basis b_n -> values at the n^3
+ * common zeros), "inverse" is x = D^{-1} y (the inverse of the CRT
+ * isomorphism of Lemma 2, which exists because the zeros are distinct) and
+ * "adjoint" is D^H g.  No normalisation beyond the 1/24 inside T_k.
+ *
+ * Layouts.  A volume is n^3 values, index (a,b,c) at a*n*n + b*n + c (last
+ * index fastest).  Coefficient volumes are indexed (j,k,p), point volumes
+ * (i,l,q).  A batch is `batch` volumes back to back.  Complex values are
+ * interleaved (re, im) pairs of the dtype's real type.
+ *
+ *   dtype          forward in      forward out     inverse/adjoint in/out
+ *   FCC_R64        double          complex double  complex double -> double
+ *   FCC_C64        complex double  complex double  complex double -> complex
+ *   FCC_R32        float           complex float   complex float  -> float
+ *   FCC_C32        complex float   complex float   complex float  -> complex
+ *
+ * For the real dtypes the inverse returns the real part of D^{-1} y (exact
+ * when y = D x for a real x) and the adjoint returns Re(D^H g), the adjoint
+ * of the real-linear map x -> D x.
+ *
+ * Ownership and execution.  `in` and `out` are DEVICE pointers owned by the
+ * caller, 16-byte aligned, not overlapping.  Calls are asynchronous on
+ * `stream` (a cudaStream_t passed as void*; NULL = legacy default stream)
+ * and never synchronise the host.  A plan owns its device tables and
+ * workspace; it is not thread safe: use one plan from one host thread and
+ * one stream at a time.  All entry points return a status code; no C++
+ * exception crosses the ABI.
+ */
+#ifndef FCC_DCT_H
+#define FCC_DCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fcc_plan fcc_plan;
+
+typedef enum {
+    FCC_OK = 0,
+    FCC_ERR_INVALID_ARG = 1, /* NULL, misaligned or overlapping buffers, bad order/batch/dtype */
+    FCC_ERR_UNSUPPORTED = 2, /* valid request this build does not implement */
+    FCC_ERR_ALLOC = 3,       /* host or device allocation failed; nothing leaked */
+    FCC_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    FCC_ERR_TIMEOUT = 5      /* a device-side wait exceeded its bound */
+} fcc_status;
+
+typedef enum {
+    FCC_R64 = 0,
+    FCC_C64 = 1,
+    FCC_R32 = 2,
+    FCC_C32 = 3,
+    FCC_R32_TF32X3 = 4,
+    FCC_R32_BF16X3 = 5,
+    FCC_R32_BF16X6 = 6
+} fcc_dtype;
+
+/* Largest supported order n. */
+#define FCC_MAX_ORDER 512
+
+/*
+ * Build a plan for `batch` volumes of order `order` (1 <= order <=
+ * FCC_MAX_ORDER, batch >= 1) in `dtype`.  Does the host-side set-up (the
+ * orbit partition of Z_n^3 under W and its class cores, Sec. 3 / Def. 2),
+ * allocates and fills device tables on the current device.  Returns NULL
+ * on error; fcc_dct_last_error() tells why.
+ */
+fcc_plan* fcc_dct_plan(int order, int batch, int dtype);
+
+/*
+ * Plan for a ragged batch: `count` volumes whose orders are orders[0..count)
+ * stored back to back (volume v starts at sum_{u<v} orders[u]^3 values).
+ * Same layouts and dtypes as fcc_dct_plan.  `orders` is a host array read
+ * during the call only.
+ */
+fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype);
+
+/* y = D x over the plan's batch; in: coefficients, out: point values. */
+fcc_status fcc_dct_forward(fcc_plan* plan, const void* in, void* out, void* stream);
+
+/* x = D^{-1} y; in: point values (complex), out: coefficients. */
+fcc_status fcc_dct_inverse(fcc_plan* plan, const void* in, void* out, void* stream);
+
+/* x = D^H g (real dtypes: Re D^H g); in: point values (complex). */
+fcc_status fcc_dct_adjoint(fcc_plan* plan, const void* in, void* out, void* stream);
+
+/*
+ * End-to-end forms taking HOST buffers: copy `host_in` to plan-owned device
+ * memory, transform, copy the result to `host_out`, all enqueued on
+ * `stream`.  The caller synchronises `stream` before reading host_out.
+ * Pinned (page-locked) host buffers make the copies asynchronous.
+ */
+fcc_status fcc_dct_forward_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
+fcc_status fcc_dct_inverse_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
+
+/* Number of volumes, total points (sum of n^3) and element counts of the
+ * forward input / output, for sizing buffers. */
+int fcc_dct_batch(const fcc_plan* plan);
+int64_t fcc_dct_points(const fcc_plan* plan);
+/* Bytes of the forward input and output of the whole batch. */
+int64_t fcc_dct_in_bytes(const fcc_plan* plan);
+int64_t fcc_dct_out_bytes(const fcc_plan* plan);
+
+/* Kernel launches one forward / inverse call enqueues (for reporting). */
+int fcc_dct_launches(const fcc_plan* plan, int which /* 0 fwd, 1 inv, 2 adj */);
+
+/*
+ * Optional per-kernel timing.  When enabled, every kernel launch the plan
+ * enqueues is bracketed by a pair of CUDA events on the launch stream.
+ * fcc_dct_profile_read() waits for the recorded events, then writes for up
+ * to `cap` kernel kinds their name (NUL-terminated, 48 bytes each, into
+ * names[48*i]), summed duration in milliseconds and launch count, clears
+ * the record and returns the number of kinds (or -1 on error).
+ */
+fcc_status fcc_dct_profile_enable(fcc_plan* plan, int enable);
+int fcc_dct_profile_read(fcc_plan* plan, char* names, double* ms, int* launches, int cap);
+
+/* Status of the last failing call on this host thread (FCC_OK if none). */
+fcc_status fcc_dct_last_error(void);
+const char* fcc_status_string(fcc_status status);
+
+/* Release the plan's device memory.  Accepts NULL. */
+void fcc_dct_destroy(fcc_plan* plan);
+
+/*
+ * Host-only description of the orbit structure for order n (no CUDA calls;
+ * usable without a GPU).  Fills, when the pointers are non-NULL:
+ *   n_orbits, n_classes, free_class (-1 if none);
+ *   reps[n_orbits]       packed representatives k1 | k2<<10 | k3<<20,
+ *   cls[n_orbits]        class of each orbit,
+ *   wrap[n_classes*72]   wrap vectors m_h (int8 as int32), slot-major,
+ *   canon[n_classes*24]  canonical slot of each slot,
+ *   fwd/inv/adj[n_classes*576*2]  24x24 complex cores (re, im) in double.
+ * Call once with NULL arrays to learn the sizes.
+ */
+fcc_status fcc_dct_describe(int order, int64_t* n_orbits, int* n_classes, int* free_class,
+                            uint32_t* reps, int32_t* cls, int32_t* wrap, int32_t* canon,
+                            double* fwd, double* inv, double* adj);
+
+/* The 24 group matrices (row-major 3x3 each) the library uses. */
+fcc_status fcc_dct_weyl_group(int32_t* out /* 216 */);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCC_DCT_H */

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libfccdct (include/fcc_dct.h).
+
+Argument marshalling only: tensors are passed as device pointers together
+with torch's current CUDA stream; every step of the transform runs in the
+library's CUDA kernels.  If the library is missing this module raises --
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfccdct.so")
+
+FCC_OK, FCC_ERR_INVALID_ARG, FCC_ERR_UNSUPPORTED, FCC_ERR_ALLOC, FCC_ERR_CUDA, FCC_ERR_TIMEOUT = range(6)
+DTYPES = {"r64": 0, "c64": 1, "r32": 2, "c32": 3, "r32_tf32x3": 4, "r32_bf16x3": 5, "r32_bf16x6": 6}
+EXPORTS = [
+    "fcc_dct_plan", "fcc_dct_plan_ragged", "fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint",
+    "fcc_dct_forward_host", "fcc_dct_inverse_host", "fcc_dct_batch", "fcc_dct_points",
+    "fcc_dct_in_bytes", "fcc_dct_out_bytes", "fcc_dct_launches", "fcc_dct_last_error",
+    "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
+    "fcc_dct_profile_enable", "fcc_dct_profile_read",
+]
+
+_LIB = None
+
+
+class FccError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfccdct.so is not built (run __graft_entry__.build()); "
+                               "there is no fallback implementation")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.fcc_dct_plan.argtypes = [i32, i32, i32]
+        L.fcc_dct_plan.restype = vp
+        L.fcc_dct_plan_ragged.argtypes = [ctypes.POINTER(i32), i32, i32]
+        L.fcc_dct_plan_ragged.restype = vp
+        for f in ("fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint", "fcc_dct_forward_host",
+                  "fcc_dct_inverse_host"):
+            getattr(L, f).argtypes = [vp, vp, vp, vp]
+            getattr(L, f).restype = i32
+        L.fcc_dct_batch.argtypes = [vp]
+        L.fcc_dct_batch.restype = i32
+        for f in ("fcc_dct_points", "fcc_dct_in_bytes", "fcc_dct_out_bytes"):
+            getattr(L, f).argtypes = [vp]
+            getattr(L, f).restype = i64
+        L.fcc_dct_launches.argtypes = [vp, i32]
+        L.fcc_dct_launches.restype = i32
+        L.fcc_dct_last_error.argtypes = []
+        L.fcc_dct_last_error.restype = i32
+        L.fcc_status_string.argtypes = [i32]
+        L.fcc_status_string.restype = ctypes.c_char_p
+        L.fcc_dct_destroy.argtypes = [vp]
+        L.fcc_dct_destroy.restype = None
+        L.fcc_dct_describe.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                       vp, vp, vp, vp, vp, vp, vp]
+        L.fcc_dct_describe.restype = i32
+        L.fcc_dct_weyl_group.argtypes = [vp]
+        L.fcc_dct_weyl_group.restype = i32
+        L.fcc_dct_profile_enable.argtypes = [vp, i32]
+        L.fcc_dct_profile_enable.restype = i32
+        L.fcc_dct_profile_read.argtypes = [vp, vp, vp, vp, i32]
+        L.fcc_dct_profile_read.restype = i32
+        _LIB = L
+    return _LIB
+
+
+def status_string(s):
+    return lib().fcc_status_string(int(s)).decode()
+
+
+def last_error():
+    return lib().fcc_dct_last_error()
+
+
+def _check(status, what):
+    if status != FCC_OK:
+        raise FccError(status, what)
+
+
+def describe(order):
+    """Host-side orbit tables of the plan builder (no GPU needed)."""
+    L = lib()
+    no, nc, fc = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    _check(L.fcc_dct_describe(order, ctypes.byref(no), ctypes.byref(nc), ctypes.byref(fc),
+                              None, None, None, None, None, None, None), "describe")
+    reps = np.zeros(no.value, dtype=np.uint32)
+    cls = np.zeros(no.value, dtype=np.int32)
+    wrap = np.zeros(nc.value * 72, dtype=np.int32)
+    canon = np.zeros(nc.value * 24, dtype=np.int32)
+    mats = [np.zeros(nc.value * 576 * 2) for _ in range(3)]
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(L.fcc_dct_describe(order, ctypes.byref(no), ctypes.byref(nc), ctypes.byref(fc), ptr(reps),
+                              ptr(cls), ptr(wrap), ptr(canon), ptr(mats[0]), ptr(mats[1]), ptr(mats[2])),
+           "describe")
+    cx = [(m[0::2] + 1j * m[1::2]).reshape(nc.value, 24, 24) for m in mats]
+    k = np.stack([reps & 1023, (reps >> 10) & 1023, (reps >> 20) & 1023], 1).astype(np.int64)
+    return {"reps": k, "cls": cls, "free_class": fc.value, "wrap": wrap.reshape(-1, 24, 3),
+            "canon": canon.reshape(-1, 24), "fwd": cx[0], "inv": cx[1], "adj": cx[2]}
+
+
+def weyl_group():
+    out = np.zeros(216, dtype=np.int32)
+    _check(lib().fcc_dct_weyl_group(out.ctypes.data_as(ctypes.c_void_p)), "weyl_group")
+    return out.reshape(24, 3, 3).astype(np.int64)
+
+
+_REAL_T = {0: "float64", 1: "float64", 2: "float32", 3: "float32", 4: "float32", 5: "float32", 6: "float32"}
+
+
+class Plan:
+    """A device plan for `batch` volumes of order `order` (or a ragged list of
+    orders).  Owns the library handle; release with close() or `with`."""
+
+    def __init__(self, order=None, batch=1, dtype="r32", orders=None):
+        import torch  # noqa: F401  (initialises the CUDA context torch uses)
+        L = lib()
+        self.dtype_code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        if orders is not None:
+            arr = (ctypes.c_int * len(orders))(*[int(o) for o in orders])
+            h = L.fcc_dct_plan_ragged(arr, len(orders), self.dtype_code)
+            self.orders = [int(o) for o in orders]
+        else:
+            h = L.fcc_dct_plan(int(order), int(batch), self.dtype_code)
+            self.orders = [int(order)] * int(batch)
+        if not h:
+            raise FccError(L.fcc_dct_last_error(), "fcc_dct_plan")
+        self.handle = ctypes.c_void_p(h)
+        self.batch = L.fcc_dct_batch(self.handle)
+        self.points = L.fcc_dct_points(self.handle)
+        self.real_input = self.dtype_code not in (1, 3)
+        self.real_type = _REAL_T[self.dtype_code]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fcc_dct_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launches(self, which=0):
+        return lib().fcc_dct_launches(self.handle, which)
+
+    def profile(self, enable=True):
+        _check(lib().fcc_dct_profile_enable(self.handle, 1 if enable else 0), "profile_enable")
+
+    def profile_read(self, cap=32):
+        """{kernel name: (total ms, launches)} recorded since the last read."""
+        names = ctypes.create_string_buffer(48 * cap)
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_int * cap)()
+        k = lib().fcc_dct_profile_read(self.handle, names, ms, cnt, cap)
+        if k < 0:
+            raise FccError(last_error(), "profile_read")
+        raw = names.raw
+        return {raw[48 * i:48 * i + 48].split(b"\0")[0].decode(): (ms[i], cnt[i]) for i in range(min(k, cap))}
+
+    # -- tensor helpers -------------------------------------------------------
+    def _torch_types(self):
+        import torch
+        rt = torch.float64 if self.real_type == "float64" else torch.float32
+        ct = torch.complex128 if rt == torch.float64 else torch.complex64
+        return rt, ct
+
+    def _shape_out(self, t, complex_):
+        import torch
+        rt, ct = self._torch_types()
+        return torch.empty(self.points, dtype=ct if complex_ else rt, device=t.device)
+
+    def _call(self, fn, what, x, out, out_complex):
+        import torch
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("input must be a contiguous CUDA tensor")
+        if out is None:
+            out = self._shape_out(x, out_complex)
+        st = torch.cuda.current_stream(x.device).cuda_stream
+        _check(fn(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                  ctypes.c_void_p(st)), what)
+        return out
+
+    def forward(self, x, out=None):
+        rt, ct = self._torch_types()
+        want = rt if self.real_input else ct
+        if x.dtype != want or x.numel() != self.points:
+            raise ValueError("forward input must be %s with %d elements" % (want, self.points))
+        return self._call(lib().fcc_dct_forward, "fcc_dct_forward", x, out, True)
+
+    def inverse(self, y, out=None):
+        rt, ct = self._torch_types()
+        if y.dtype != ct or y.numel() != self.points:
+            raise ValueError("inverse input must be %s with %d elements" % (ct, self.points))
+        return self._call(lib().fcc_dct_inverse, "fcc_dct_inverse", y, out, not self.real_input)
+
+    def adjoint(self, g, out=None):
+        rt, ct = self._torch_types()
+        if g.dtype != ct or g.numel() != self.points:
+            raise ValueError("adjoint input must be %s with %d elements" % (ct, self.points))
+        return self._call(lib().fcc_dct_adjoint, "fcc_dct_adjoint", g, out, not self.real_input)
+
+    def forward_host(self, x_host, y_host):
+        """End-to-end call with host tensors (pinned for async copies); the
+        caller synchronises the current stream before reading y_host."""
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        _check(lib().fcc_dct_forward_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
+                                          ctypes.c_void_p(y_host.data_ptr()), ctypes.c_void_p(st)),
+               "fcc_dct_forward_host")
+        return y_host

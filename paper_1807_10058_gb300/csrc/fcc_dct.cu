@@ -1,0 +1,545 @@
+// C ABI of libfccdct (declared in include/fcc_dct.h): plans, launches,
+// error handling.  All compute runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fcc_dct.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+using namespace fcc;
+
+namespace {
+
+thread_local fcc_status g_last = FCC_OK;
+
+fcc_status fail(fcc_status s) {
+    g_last = s;
+    return s;
+}
+
+bool is_double(int dtype) { return dtype == FCC_R64 || dtype == FCC_C64; }
+bool is_real_in(int dtype) { return dtype != FCC_C64 && dtype != FCC_C32; }
+
+// Device copy of one order's tables.
+struct OrderTables {
+    int n = 0;
+    int64_t n_orbits = 0;
+    int n_classes = 0;
+    std::vector<int> radices;
+    uint32_t* reps = nullptr;
+    uint8_t* cls = nullptr;
+    int8_t* wrap = nullptr;
+    uint32_t* canon_mask = nullptr;
+    void* mat[3] = {nullptr, nullptr, nullptr};  // fwd, inv, adj
+    void* phase = nullptr;                        // [8n] complex
+    void* tw = nullptr;                           // [n] complex, exp(+2 pi i j / n)
+};
+
+}  // namespace
+
+struct fcc_plan {
+    int device = 0;
+    int dtype = 0;
+    int batch = 0;
+    bool uniform = true;
+    std::vector<int> orders;         // per volume
+    std::vector<int64_t> offset;     // point offset of each volume
+    int64_t points = 0;
+    std::map<int, OrderTables> tabs;
+    void* scratch = nullptr;         // complex workspace for inverse / adjoint
+    int64_t scratch_points = 0;
+    void* host_in_dev = nullptr;     // device staging for the *_host entry points
+    void* host_out_dev = nullptr;
+    std::vector<void*> allocs;
+    // per-kernel timing (fcc_dct_profile_enable)
+    bool profiling = false;
+    struct Rec { const char* name; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+size_t real_size(int dtype) { return is_double(dtype) ? 8 : 4; }
+
+template <typename T>
+std::vector<T> to_pairs(const std::vector<cd>& v) {
+    std::vector<T> out(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        out[2 * i] = (T)v[i].real();
+        out[2 * i + 1] = (T)v[i].imag();
+    }
+    return out;
+}
+
+fcc_status dev_alloc(fcc_plan* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return FCC_OK;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return FCC_ERR_ALLOC;
+    }
+    p->allocs.push_back(*ptr);
+    return FCC_OK;
+}
+
+fcc_status upload(fcc_plan* p, void** ptr, const void* src, size_t bytes) {
+    fcc_status s = dev_alloc(p, ptr, bytes);
+    if (s != FCC_OK) return s;
+    if (bytes && cudaMemcpy(*ptr, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return FCC_ERR_CUDA;
+    return FCC_OK;
+}
+
+template <typename T>
+fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
+    HostPlan hp;
+    const int rc = build_host_plan(n, hp);
+    if (rc == -1) return FCC_ERR_INVALID_ARG;
+    if (rc != 0) return FCC_ERR_UNSUPPORTED;
+    t.n = n;
+    t.n_orbits = (int64_t)hp.reps.size();
+    t.n_classes = (int)hp.classes.size();
+    t.radices = fft_radices(n);
+    if ((int)t.radices.size() > kMaxStages) return FCC_ERR_UNSUPPORTED;
+    for (int r : t.radices)
+        if (r > 31) return FCC_ERR_UNSUPPORTED;
+    std::vector<int8_t> wrap(72 * t.n_classes);
+    std::vector<uint32_t> cm(t.n_classes);
+    std::vector<cd> mats[3];
+    for (int c = 0; c < t.n_classes; ++c) {
+        const OrbitClass& oc = hp.classes[c];
+        std::memcpy(&wrap[72 * c], oc.wrap, 72);
+        cm[c] = oc.canon_mask;
+        mats[0].insert(mats[0].end(), oc.fwd.begin(), oc.fwd.end());
+        mats[1].insert(mats[1].end(), oc.inv.begin(), oc.inv.end());
+        mats[2].insert(mats[2].end(), oc.adj.begin(), oc.adj.end());
+    }
+    std::vector<cd> phase(8 * n), tw(n);
+    for (int e = 0; e < 8 * n; ++e) phase[e] = std::polar(1.0, 2.0 * M_PI * e / (8.0 * n));
+    for (int j = 0; j < n; ++j) tw[j] = std::polar(1.0, 2.0 * M_PI * j / (double)n);
+    fcc_status s;
+    if ((s = upload(p, (void**)&t.reps, hp.reps.data(), hp.reps.size() * 4))) return s;
+    if ((s = upload(p, (void**)&t.cls, hp.cls.data(), hp.cls.size()))) return s;
+    if ((s = upload(p, (void**)&t.wrap, wrap.data(), wrap.size()))) return s;
+    if ((s = upload(p, (void**)&t.canon_mask, cm.data(), cm.size() * 4))) return s;
+    for (int m = 0; m < 3; ++m) {
+        auto v = to_pairs<T>(mats[m]);
+        if ((s = upload(p, &t.mat[m], v.data(), v.size() * sizeof(T)))) return s;
+    }
+    auto ph = to_pairs<T>(phase);
+    if ((s = upload(p, &t.phase, ph.data(), ph.size() * sizeof(T)))) return s;
+    auto twv = to_pairs<T>(tw);
+    if ((s = upload(p, &t.tw, twv.data(), twv.size() * sizeof(T)))) return s;
+    return FCC_OK;
+}
+
+fcc_status upload_group() {
+    const WeylGroup& G = weyl();
+    if (cudaMemcpyToSymbol(c_W, G.m, sizeof(G.m)) != cudaSuccess) return FCC_ERR_CUDA;
+    if (cudaMemcpyToSymbol(c_u, G.u, sizeof(G.u)) != cudaSuccess) return FCC_ERR_CUDA;
+    return FCC_OK;
+}
+
+void release(fcc_plan* p) {
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    for (void* a : p->allocs) cudaFree(a);
+    for (auto& r : p->recs) { if (r.a) cudaEventDestroy(r.a); if (r.b) cudaEventDestroy(r.b); }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
+    if (dtype < FCC_R64 || dtype > FCC_R32_BF16X6) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    if (dtype > FCC_C32) { fail(FCC_ERR_UNSUPPORTED); return nullptr; }
+    if (orders.empty()) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    for (int n : orders)
+        if (n < 1 || n > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    fcc_plan* p = new (std::nothrow) fcc_plan();
+    if (!p) { fail(FCC_ERR_ALLOC); return nullptr; }
+    if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); delete p; fail(FCC_ERR_CUDA); return nullptr; }
+    p->dtype = dtype;
+    p->batch = (int)orders.size();
+    p->orders = orders;
+    p->uniform = std::all_of(orders.begin(), orders.end(), [&](int n) { return n == orders[0]; });
+    int64_t off = 0;
+    int64_t maxpts = 0;
+    for (int n : orders) {
+        p->offset.push_back(off);
+        const int64_t n3 = (int64_t)n * n * n;
+        off += n3;
+        maxpts = std::max(maxpts, n3);
+    }
+    p->points = off;
+    fcc_status s = upload_group();
+    for (int n : orders) {
+        if (s != FCC_OK) break;
+        if (p->tabs.count(n)) continue;
+        OrderTables t;
+        s = is_double(dtype) ? build_tables<double>(p, n, t) : build_tables<float>(p, n, t);
+        p->tabs[n] = t;
+    }
+    if (s == FCC_OK) {
+        // workspace: enough whole volumes for ~64 MB, at least one volume
+        const int64_t bytes_per_pt = 2 * real_size(dtype);
+        int64_t chunk_pts = std::max<int64_t>(maxpts, (int64_t(64) << 20) / bytes_per_pt);
+        chunk_pts = std::min<int64_t>(chunk_pts, p->points);
+        p->scratch_points = chunk_pts;
+        s = dev_alloc(p, &p->scratch, chunk_pts * bytes_per_pt);
+    }
+    if (s != FCC_OK) {
+        release(p);
+        fail(s);
+        return nullptr;
+    }
+    return p;
+}
+
+// --- optional per-kernel events ------------------------------------------
+
+thread_local fcc_plan* g_prof_plan = nullptr;  // plan whose launches are being recorded
+
+cudaEvent_t take_event(fcc_plan* p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+struct ProfScope {
+    fcc_plan* p;
+    fcc_plan::Rec r{nullptr, nullptr, nullptr};
+    cudaStream_t st;
+    ProfScope(const char* name, cudaStream_t s) : p(g_prof_plan), st(s) {
+        if (!p || !p->profiling) { p = nullptr; return; }
+        r.name = name;
+        r.a = take_event(p);
+        r.b = take_event(p);
+        if (r.a) cudaEventRecord(r.a, st);
+    }
+    ~ProfScope() {
+        if (!p) return;
+        if (r.b) cudaEventRecord(r.b, st);
+        p->recs.push_back(r);
+    }
+};
+
+// --- launches -------------------------------------------------------------
+
+template <typename T>
+fcc_status launch_fft(const OrderTables& t, const T* in, T* out, int64_t nvol, int axis, int sign,
+                      cudaStream_t st) {
+    const int n = t.n;
+    if (n == 1) {
+        if (in != out) cudaMemcpyAsync(out, in, nvol * 2 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+    }
+    FftArgs a{};
+    a.n = n;
+    a.nstages = (int)t.radices.size();
+    for (int s = 0; s < a.nstages; ++s) a.radix[s] = t.radices[s];
+    a.axis = axis;
+    const int budget = (int)((sizeof(T) == 4 ? 4096 : 2048));
+    a.P = std::max(1, budget / n);
+    if (axis != 2) a.P = std::min(a.P, n);
+    a.nvol = nvol;
+    a.sign = sign;
+    int64_t tiles;
+    if (axis == 2) tiles = (nvol * n * n + a.P - 1) / a.P;
+    else tiles = nvol * n * ((n + a.P - 1) / a.P);
+    const size_t smem = (size_t)(4 * a.P * (n + 1) + 2 * n) * sizeof(T);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(T) == 8]) {
+        cudaFuncSetAttribute(fft_axis_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set[sizeof(T) == 8] = true;
+    }
+    if (tiles > 0x7fffffffLL) return FCC_ERR_UNSUPPORTED;
+    static const char* names[3] = {"fft_axis0", "fft_axis1", "fft_axis2"};
+    ProfScope ps(names[axis], st);
+    fft_axis_kernel<T><<<(unsigned)tiles, 256, smem, st>>>(in, out, (const T*)t.tw, a);
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
+template <typename T>
+fcc_status launch_mix(const OrderTables& t, int mode, bool real_in, bool real_out, const T* in, T* out,
+                      int64_t nvol, T scale, cudaStream_t st) {
+    MixArgs<T> a;
+    a.reps = t.reps;
+    a.cls = t.cls;
+    a.mats = (const T*)t.mat[mode];
+    a.wrap = t.wrap;
+    a.canon_mask = t.canon_mask;
+    a.phase = (const T*)t.phase;
+    a.n = t.n;
+    a.n_orbits = t.n_orbits;
+    a.n3 = (int64_t)t.n * t.n * t.n;
+    a.scale = scale;
+    const unsigned bx = (unsigned)((t.n_orbits + 127) / 128);
+    for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
+        const int64_t nv = std::min<int64_t>(65535, nvol - v0);
+        dim3 grid(bx, (unsigned)nv);
+        static const char* names[3] = {"orbit_mix_fwd", "orbit_mix_inv", "orbit_mix_adj"};
+        ProfScope ps(names[mode], st);
+        const T* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
+        T* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
+        if (mode == MODE_FWD) {
+            if (real_in) orbit_mix_kernel<T, MODE_FWD, true, false><<<grid, 128, 0, st>>>(src, dst, a);
+            else orbit_mix_kernel<T, MODE_FWD, false, false><<<grid, 128, 0, st>>>(src, dst, a);
+        } else if (mode == MODE_INV) {
+            if (real_out) orbit_mix_kernel<T, MODE_INV, false, true><<<grid, 128, 0, st>>>(src, dst, a);
+            else orbit_mix_kernel<T, MODE_INV, false, false><<<grid, 128, 0, st>>>(src, dst, a);
+        } else {
+            if (real_out) orbit_mix_kernel<T, MODE_ADJ, false, true><<<grid, 128, 0, st>>>(src, dst, a);
+            else orbit_mix_kernel<T, MODE_ADJ, false, false><<<grid, 128, 0, st>>>(src, dst, a);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
+// Run a group of `nvol` consecutive volumes of the same order.
+template <typename T>
+fcc_status run_group(fcc_plan* p, int which, const OrderTables& t, const T* in, T* out, int64_t nvol,
+                     cudaStream_t st) {
+    const bool rin = is_real_in(p->dtype);
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    fcc_status s = FCC_OK;
+    if (which == 0) {
+        // Z = S x into out, then F along the three axes in place.
+        if ((s = launch_mix<T>(t, MODE_FWD, rin, false, in, out, nvol, T(1), st))) return s;
+        for (int ax = 2; ax >= 0 && !s; --ax) s = launch_fft<T>(t, out, out, nvol, ax, +1, st);
+        return s;
+    }
+    // inverse / adjoint: conj-sign DFT into the workspace, then the orbit map
+    const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
+    const T scale = which == 1 ? T(1.0 / (double)n3) : T(1);
+    const int64_t in_stride = 2 * n3;
+    const int64_t out_stride = (rin ? 1 : 2) * n3;
+    T* ws = (T*)p->scratch;
+    for (int64_t v0 = 0; v0 < nvol && !s; v0 += chunk) {
+        const int64_t nv = std::min(chunk, nvol - v0);
+        const T* src = in + v0 * in_stride;
+        s = launch_fft<T>(t, src, ws, nv, 0, -1, st);
+        if (!s) s = launch_fft<T>(t, ws, ws, nv, 1, -1, st);
+        if (!s) s = launch_fft<T>(t, ws, ws, nv, 2, -1, st);
+        if (!s) s = launch_mix<T>(t, which == 1 ? MODE_INV : MODE_ADJ, false, rin, ws, out + v0 * out_stride, nv, scale, st);
+    }
+    return s;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int64_t in_bytes(const fcc_plan* p, int which) {
+    const int64_t rs = real_size(p->dtype);
+    if (which == 0) return p->points * rs * (is_real_in(p->dtype) ? 1 : 2);
+    return p->points * rs * 2;
+}
+int64_t out_bytes(const fcc_plan* p, int which) {
+    const int64_t rs = real_size(p->dtype);
+    if (which == 0) return p->points * rs * 2;
+    return p->points * rs * (is_real_in(p->dtype) ? 1 : 2);
+}
+
+template <typename T>
+fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t st) {
+    const T* in = (const T*)vin;
+    T* out = (T*)vout;
+    const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
+    const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
+    fcc_status s = FCC_OK;
+    int v = 0;
+    while (v < p->batch && !s) {
+        int e = v + 1;
+        while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
+        const OrderTables& t = p->tabs.at(p->orders[v]);
+        s = run_group<T>(p, which, t, in + p->offset[v] * rs_in, out + p->offset[v] * rs_out, e - v, st);
+        v = e;
+    }
+    return s;
+}
+
+fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* stream) {
+    if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
+    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, which);
+    const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, which);
+    if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    g_prof_plan = p;
+    fcc_status s = is_double(p->dtype) ? run<double>(p, which, in, out, st) : run<float>(p, which, in, out, st);
+    g_prof_plan = nullptr;
+    if (cur != p->device) cudaSetDevice(cur);
+    return s == FCC_OK ? FCC_OK : fail(s);
+}
+
+fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream) {
+    if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ib = in_bytes(p, which), ob = out_bytes(p, which);
+    const int64_t cap = std::max(in_bytes(p, 0), in_bytes(p, 1));
+    const int64_t capo = std::max(out_bytes(p, 0), out_bytes(p, 1));
+    fcc_status s;
+    if (!p->host_in_dev && (s = dev_alloc(p, &p->host_in_dev, cap))) return fail(s);
+    if (!p->host_out_dev && (s = dev_alloc(p, &p->host_out_dev, capo))) return fail(s);
+    if (cudaMemcpyAsync(p->host_in_dev, hin, ib, cudaMemcpyHostToDevice, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
+    if ((s = dispatch(p, which, p->host_in_dev, p->host_out_dev, stream))) return s;
+    if (cudaMemcpyAsync(hout, p->host_out_dev, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
+    return FCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fcc_plan* fcc_dct_plan(int order, int batch, int dtype) {
+    if (batch < 1 || order < 1 || order > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    return make_plan(std::vector<int>((size_t)batch, order), dtype);
+}
+
+fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype) {
+    if (!orders || count < 1) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    return make_plan(std::vector<int>(orders, orders + count), dtype);
+}
+
+fcc_status fcc_dct_forward(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 0, in, out, stream); }
+fcc_status fcc_dct_inverse(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 1, in, out, stream); }
+fcc_status fcc_dct_adjoint(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 2, in, out, stream); }
+fcc_status fcc_dct_forward_host(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_host(p, 0, in, out, stream); }
+fcc_status fcc_dct_inverse_host(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_host(p, 1, in, out, stream); }
+
+int fcc_dct_batch(const fcc_plan* p) { return p ? p->batch : 0; }
+int64_t fcc_dct_points(const fcc_plan* p) { return p ? p->points : 0; }
+int64_t fcc_dct_in_bytes(const fcc_plan* p) { return p ? in_bytes(p, 0) : 0; }
+int64_t fcc_dct_out_bytes(const fcc_plan* p) { return p ? out_bytes(p, 0) : 0; }
+
+int fcc_dct_launches(const fcc_plan* p, int which) {
+    if (!p) return 0;
+    int total = 0;
+    int v = 0;
+    while (v < p->batch) {
+        int e = v + 1;
+        while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
+        const int n = p->orders[v];
+        const int64_t n3 = (int64_t)n * n * n;
+        const int64_t nv = e - v;
+        const int mix = (int)((nv + 65534) / 65535);
+        if (which == 0) total += mix + 3;
+        else {
+            const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
+            total += (int)((nv + chunk - 1) / chunk) * 4;
+        }
+        v = e;
+    }
+    return total;
+}
+
+fcc_status fcc_dct_profile_enable(fcc_plan* p, int enable) {
+    if (!p) return fail(FCC_ERR_INVALID_ARG);
+    p->profiling = enable != 0;
+    return FCC_OK;
+}
+
+int fcc_dct_profile_read(fcc_plan* p, char* names, double* ms, int* launches, int cap) {
+    if (!p || cap < 0) { fail(FCC_ERR_INVALID_ARG); return -1; }
+    std::vector<std::string> kinds;
+    std::vector<double> tot;
+    std::vector<int> cnt;
+    for (auto& r : p->recs) {
+        float t = 0.f;
+        if (r.a && r.b) {
+            if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+                cudaGetLastError();
+                t = 0.f;
+            }
+        }
+        size_t k = 0;
+        while (k < kinds.size() && kinds[k] != r.name) ++k;
+        if (k == kinds.size()) { kinds.push_back(r.name); tot.push_back(0); cnt.push_back(0); }
+        tot[k] += t;
+        cnt[k] += 1;
+        if (r.a) p->event_pool.push_back(r.a);
+        if (r.b) p->event_pool.push_back(r.b);
+    }
+    p->recs.clear();
+    for (size_t k = 0; k < kinds.size() && (int)k < cap; ++k) {
+        if (names) { std::strncpy(names + 48 * k, kinds[k].c_str(), 47); names[48 * k + 47] = 0; }
+        if (ms) ms[k] = tot[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    return (int)kinds.size();
+}
+
+fcc_status fcc_dct_last_error(void) { return g_last; }
+
+const char* fcc_status_string(fcc_status s) {
+    switch (s) {
+        case FCC_OK: return "ok";
+        case FCC_ERR_INVALID_ARG: return "invalid argument";
+        case FCC_ERR_UNSUPPORTED: return "unsupported";
+        case FCC_ERR_ALLOC: return "allocation failed";
+        case FCC_ERR_CUDA: return "CUDA error";
+        case FCC_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+void fcc_dct_destroy(fcc_plan* p) { release(p); }
+
+fcc_status fcc_dct_describe(int order, int64_t* n_orbits, int* n_classes, int* free_class, uint32_t* reps,
+                            int32_t* cls, int32_t* wrap, int32_t* canon, double* fwd, double* inv,
+                            double* adj) {
+    HostPlan hp;
+    const int rc = build_host_plan(order, hp);
+    if (rc == -1) return fail(FCC_ERR_INVALID_ARG);
+    if (rc != 0) return fail(FCC_ERR_UNSUPPORTED);
+    if (n_orbits) *n_orbits = (int64_t)hp.reps.size();
+    if (n_classes) *n_classes = (int)hp.classes.size();
+    if (free_class) *free_class = hp.free_class;
+    for (size_t o = 0; o < hp.reps.size(); ++o) {
+        if (reps) reps[o] = hp.reps[o];
+        if (cls) cls[o] = hp.cls[o];
+    }
+    for (size_t c = 0; c < hp.classes.size(); ++c) {
+        const OrbitClass& oc = hp.classes[c];
+        for (int h = 0; h < 24; ++h) {
+            if (canon) canon[24 * c + h] = oc.canon[h];
+            for (int i = 0; i < 3; ++i)
+                if (wrap) wrap[72 * c + 3 * h + i] = oc.wrap[h][i];
+        }
+        for (int e = 0; e < 576; ++e) {
+            if (fwd) { fwd[2 * (576 * c + e)] = oc.fwd[e].real(); fwd[2 * (576 * c + e) + 1] = oc.fwd[e].imag(); }
+            if (inv) { inv[2 * (576 * c + e)] = oc.inv[e].real(); inv[2 * (576 * c + e) + 1] = oc.inv[e].imag(); }
+            if (adj) { adj[2 * (576 * c + e)] = oc.adj[e].real(); adj[2 * (576 * c + e) + 1] = oc.adj[e].imag(); }
+        }
+    }
+    return FCC_OK;
+}
+
+fcc_status fcc_dct_weyl_group(int32_t* out) {
+    if (!out) return fail(FCC_ERR_INVALID_ARG);
+    const WeylGroup& G = weyl();
+    for (int g = 0; g < 24; ++g)
+        for (int j = 0; j < 9; ++j) out[9 * g + j] = G.m[g][j];
+    return FCC_OK;
+}
+
+}  // extern "C"

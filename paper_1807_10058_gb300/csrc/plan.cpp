@@ -1,0 +1,272 @@
+// Host-side plan builder: W, orbit partition of Z_n^3, class cores.
+// See plan.h for the factorisation it implements.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace fcc {
+
+namespace {
+
+// Generators of Sec. 3 (row-major).
+const int kGen[3][9] = {
+    {-1, 0, 0, 1, 1, 0, 0, 0, 1},
+    {1, 1, 0, 0, -1, 0, 0, 1, 1},
+    {1, 0, 0, 0, 1, 1, 0, 0, -1},
+};
+const int kV[3] = {1, 0, 3};  // 8 * (1/8, 0, 3/8)
+
+void mat3(const int* a, const int* b, int* c) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            int s = 0;
+            for (int k = 0; k < 3; ++k) s += a[3 * i + k] * b[3 * k + j];
+            c[3 * i + j] = s;
+        }
+}
+
+WeylGroup make_weyl() {
+    WeylGroup G{};
+    std::vector<std::array<int, 9>> els;
+    els.push_back({1, 0, 0, 0, 1, 0, 0, 0, 1});
+    for (size_t head = 0; head < els.size(); ++head)
+        for (int g = 0; g < 3; ++g) {
+            std::array<int, 9> c;
+            mat3(kGen[g], els[head].data(), c.data());
+            if (std::find(els.begin(), els.end(), c) == els.end()) els.push_back(c);
+        }
+    // |W| = 24 for the printed generators; anything else is a build error.
+    if (els.size() != 24) std::abort();
+    for (int a = 0; a < 24; ++a) std::memcpy(G.m[a], els[a].data(), sizeof(G.m[a]));
+    auto find = [&](const int* c) {
+        for (int j = 0; j < 24; ++j)
+            if (std::memcmp(c, G.m[j], sizeof(int) * 9) == 0) return j;
+        std::abort();
+    };
+    for (int a = 0; a < 24; ++a)
+        for (int b = 0; b < 24; ++b) {
+            int c[9];
+            mat3(G.m[a], G.m[b], c);
+            G.mul[a][b] = find(c);
+        }
+    for (int a = 0; a < 24; ++a)
+        for (int b = 0; b < 24; ++b)
+            if (G.mul[a][b] == 0) G.inv[a] = b;
+    for (int g = 0; g < 24; ++g)
+        for (int j = 0; j < 3; ++j) {
+            int s = 0;
+            for (int i = 0; i < 3; ++i) s += G.m[g][3 * i + j] * kV[i];
+            G.u[g][j] = s;
+        }
+    return G;
+}
+
+// exact 8th roots of unity w_8^e
+cd root8(int e) {
+    e = ((e % 8) + 8) % 8;
+    const double h = std::sqrt(0.5);
+    static const double re[8] = {1, 0, 0, 0, -1, 0, 0, 0};
+    static const double im[8] = {0, 0, 1, 0, 0, 0, -1, 0};
+    if (e % 2 == 0) return cd(re[e], im[e]);
+    const double sr = (e == 1 || e == 7) ? h : -h;
+    const double si = (e == 1 || e == 3) ? h : -h;
+    return cd(sr, si);
+}
+
+// Gauss-Jordan inverse with partial pivoting; returns false if singular.
+bool invert(std::vector<cd>& a, int s) {
+    std::vector<cd> inv(s * s, cd(0));
+    for (int i = 0; i < s; ++i) inv[i * s + i] = 1;
+    for (int c = 0; c < s; ++c) {
+        int p = c;
+        for (int r = c + 1; r < s; ++r)
+            if (std::abs(a[r * s + c]) > std::abs(a[p * s + c])) p = r;
+        if (std::abs(a[p * s + c]) < 1e-12) return false;
+        if (p != c)
+            for (int j = 0; j < s; ++j) {
+                std::swap(a[p * s + j], a[c * s + j]);
+                std::swap(inv[p * s + j], inv[c * s + j]);
+            }
+        cd d = cd(1) / a[c * s + c];
+        for (int j = 0; j < s; ++j) {
+            a[c * s + j] *= d;
+            inv[c * s + j] *= d;
+        }
+        for (int r = 0; r < s; ++r)
+            if (r != c && a[r * s + c] != cd(0)) {
+                cd f = a[r * s + c];
+                for (int j = 0; j < s; ++j) {
+                    a[r * s + j] -= f * a[c * s + j];
+                    inv[r * s + j] -= f * inv[c * s + j];
+                }
+            }
+    }
+    a.swap(inv);
+    return true;
+}
+
+using ClassKey = std::array<int8_t, 24 * 4>;
+
+}  // namespace
+
+const WeylGroup& weyl() {
+    static const WeylGroup G = make_weyl();
+    return G;
+}
+
+std::vector<int> fft_radices(int n) {
+    std::vector<int> r;
+    while (n % 4 == 0) { r.push_back(4); n /= 4; }
+    while (n % 2 == 0) { r.push_back(2); n /= 2; }
+    for (int p : {3, 5, 7, 11, 13}) {
+        while (n % p == 0) { r.push_back(p); n /= p; }
+    }
+    if (n > 1) r.push_back(n);  // larger prime: generic radix
+    return r;
+}
+
+int build_host_plan(int n, HostPlan& P) {
+    if (n < 1 || n > kMaxOrder) return -1;
+    const WeylGroup& G = weyl();
+    P = HostPlan();
+    P.n = n;
+    P.points = (int64_t)n * n * n;
+    std::vector<uint8_t> seen(P.points, 0);
+    std::map<ClassKey, int> key2cls;
+    std::vector<uint32_t> reps;
+    std::vector<int> cls;
+    int64_t covered = 0;
+
+    for (int k1 = 0; k1 <= n; ++k1)
+        for (int k2 = 0; k1 + k2 <= n; ++k2)
+            for (int k3 = 0; k1 + k2 + k3 <= n; ++k3) {
+                const int k[3] = {k1, k2, k3};
+                int64_t flat[24];
+                ClassKey key;
+                int8_t canon[24];
+                for (int h = 0; h < 24; ++h) {
+                    int kap[3];
+                    for (int i = 0; i < 3; ++i) {
+                        const int p = G.m[h][3 * i] * k[0] + G.m[h][3 * i + 1] * k[1] + G.m[h][3 * i + 2] * k[2];
+                        kap[i] = ((p % n) + n) % n;
+                        key[3 * h + i] = (int8_t)((p - kap[i]) / n);
+                    }
+                    flat[h] = ((int64_t)kap[0] * n + kap[1]) * n + kap[2];
+                    canon[h] = (int8_t)h;
+                    for (int j = 0; j < h; ++j)
+                        if (flat[j] == flat[h]) { canon[h] = canon[j]; break; }
+                    key[72 + h] = canon[h];
+                }
+                if (seen[flat[0]]) continue;  // orbit already has a representative
+                for (int h = 0; h < 24; ++h)
+                    if (canon[h] == h) {
+                        if (seen[flat[h]]) return -2;
+                        seen[flat[h]] = 1;
+                        ++covered;
+                    }
+                auto it = key2cls.find(key);
+                int c;
+                if (it == key2cls.end()) {
+                    c = (int)P.classes.size();
+                    key2cls[key] = c;
+                    OrbitClass oc{};
+                    std::memcpy(oc.wrap, key.data(), 72);
+                    std::memcpy(oc.canon, canon, 24);
+                    P.classes.push_back(oc);
+                } else {
+                    c = it->second;
+                }
+                const bool interior = k1 > 0 && k2 > 0 && k3 > 0 && k1 + k2 + k3 < n;
+                bool all_distinct = true;
+                for (int h = 0; h < 24; ++h) all_distinct &= canon[h] == h;
+                if (interior && all_distinct) {
+                    if (P.free_class < 0) P.free_class = c;
+                    else if (P.free_class != c) return -2;  // the free core must be universal
+                }
+                reps.push_back((uint32_t)k1 | ((uint32_t)k2 << 10) | ((uint32_t)k3 << 20));
+                cls.push_back(c);
+            }
+    if (covered != P.points) return -2;
+    if (P.classes.size() > 255) return -2;
+
+    // Class cores.
+    for (auto& oc : P.classes) {
+        int s = 0;
+        oc.canon_mask = 0;
+        for (int h = 0; h < 24; ++h)
+            if (oc.canon[h] == h) {
+                oc.dist[h] = (int8_t)s++;
+                oc.canon_mask |= 1u << h;
+            }
+        for (int h = 0; h < 24; ++h) oc.dist[h] = oc.dist[oc.canon[h]];
+        oc.distinct = s;
+        oc.fwd.assign(576, cd(0));
+        for (int g = 0; g < 24; ++g)
+            for (int h = 0; h < 24; ++h) {
+                const int w = G.mul[g][G.inv[h]];
+                int t = 0;
+                for (int i = 0; i < 3; ++i) {
+                    const int wm = G.m[w][3 * i] * oc.wrap[h][0] + G.m[w][3 * i + 1] * oc.wrap[h][1] +
+                                   G.m[w][3 * i + 2] * oc.wrap[h][2];
+                    t += wm * kV[i];
+                }
+                oc.fwd[g * 24 + h] = root8(-t) / 24.0;
+            }
+        // distinct-member block B (s x s): rows at canonical slots, columns
+        // summed over slots holding the same member
+        std::vector<cd> B(s * s, cd(0));
+        for (int g = 0; g < 24; ++g) {
+            if (oc.canon[g] != g) continue;
+            for (int h = 0; h < 24; ++h) B[oc.dist[g] * s + oc.dist[h]] += oc.fwd[g * 24 + h];
+        }
+        std::vector<cd> Binv = B;
+        if (!invert(Binv, s)) return -2;
+        oc.inv.assign(576, cd(0));
+        oc.adj.assign(576, cd(0));
+        for (int h = 0; h < 24; ++h)
+            for (int g = 0; g < 24; ++g) {
+                if (oc.canon[g] != g) continue;
+                oc.inv[h * 24 + g] = Binv[oc.dist[h] * s + oc.dist[g]];
+                oc.adj[h * 24 + g] = std::conj(B[oc.dist[g] * s + oc.dist[h]]);
+            }
+    }
+
+    // Sort orbits by class (free class first), stable in enumeration order.
+    const int ncls = (int)P.classes.size();
+    std::vector<int> rank(ncls);
+    {
+        std::vector<int> order(ncls);
+        for (int c = 0; c < ncls; ++c) order[c] = c;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (a == P.free_class) > (b == P.free_class);
+        });
+        // renumber classes so that class index == rank
+        std::vector<OrbitClass> sorted(ncls);
+        for (int r = 0; r < ncls; ++r) {
+            rank[order[r]] = r;
+            sorted[r] = P.classes[order[r]];
+        }
+        P.classes.swap(sorted);
+        if (P.free_class >= 0) P.free_class = rank[P.free_class];
+    }
+    P.class_begin.assign(ncls, 0);
+    P.class_count.assign(ncls, 0);
+    for (int c : cls) P.class_count[rank[c]]++;
+    for (int c = 1; c < ncls; ++c) P.class_begin[c] = P.class_begin[c - 1] + P.class_count[c - 1];
+    std::vector<int64_t> pos = P.class_begin;
+    P.reps.resize(reps.size());
+    P.cls.resize(reps.size());
+    for (size_t o = 0; o < reps.size(); ++o) {
+        const int r = rank[cls[o]];
+        const int64_t at = pos[r]++;
+        P.reps[at] = reps[o];
+        P.cls[at] = (uint8_t)r;
+    }
+    for (int c = 0; c < ncls; ++c) P.orbits_per_class_max = std::max(P.orbits_per_class_max, P.class_count[c]);
+    return 0;
+}
+
+}  // namespace fcc

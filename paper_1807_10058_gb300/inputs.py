@@ -92,3 +92,35 @@ def bernoulli_mask(n, batch=1, seed=0, p=0.1):
     for b in range(batch):
         out[b] = _rng(seed, b).random((n, n, n)) < p
     return out
+
+
+def phantom_device(n, batch, seed=0, noise=1e-3, device="cuda"):
+    """Same recipe as ``phantom`` evaluated with torch on `device` (used for
+    benchmark-sized batches).  Ellipsoid parameters come from
+    ``default_rng(seed + b)``; the N(0, noise^2) term from a torch generator
+    seeded with seed + b.  Returns a float32 tensor of batch * n^3 values."""
+    import torch
+    out = torch.zeros(batch, n, n, n, dtype=torch.float32, device=device)
+    ax1 = torch.arange(n, device=device, dtype=torch.float32)
+    gen = torch.Generator(device=device)
+    for b in range(batch):
+        g = _rng(seed, b)
+        vol = out[b]
+        for _ in range(int(g.integers(10, 31))):
+            c = g.uniform(0.0, n, size=3)
+            ax = g.uniform(0.05 * n, 0.35 * n, size=3)
+            R = _rotation(g)
+            rho = g.uniform(0.0, 1.0)
+            half = np.sqrt(((R * ax[None, :]) ** 2).sum(1))
+            lo = np.maximum(np.floor(c - half).astype(int), 0)
+            hi = np.minimum(np.ceil(c + half).astype(int) + 1, n)
+            if np.any(hi <= lo):
+                continue
+            A = torch.tensor(R / ax[None, :], dtype=torch.float32, device=device)
+            p = torch.stack(torch.meshgrid(ax1[lo[0]:hi[0]], ax1[lo[1]:hi[1]], ax1[lo[2]:hi[2]],
+                                           indexing="ij"), -1) - torch.tensor(c, dtype=torch.float32, device=device)
+            q = p @ A
+            vol[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] += float(rho) * ((q * q).sum(-1) <= 1.0).float()
+        gen.manual_seed(int(seed) + b)
+        vol += noise * torch.randn(n, n, n, generator=gen, device=device)
+    return out.reshape(-1)

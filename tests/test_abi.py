@@ -1,0 +1,63 @@
+"""The C ABI library loads, exports what include/fcc_dct.h declares, and
+rejects bad arguments before touching the GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1807_10058_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fcc_dct.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fcc_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = binding.lib()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(binding.EXPORTS) == set(names)
+
+
+def test_status_strings():
+    for s in range(6):
+        assert binding.status_string(s)
+
+
+@pytest.mark.parametrize("order,batch,dtype", [(0, 1, 2), (-3, 1, 2), (513, 1, 2), (8, 0, 2), (8, 1, 99), (8, 1, -1)])
+def test_invalid_plan_arguments(order, batch, dtype):
+    L = binding.lib()
+    assert not L.fcc_dct_plan(order, batch, dtype)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
+
+
+def test_invalid_ragged_arguments():
+    L = binding.lib()
+    assert not L.fcc_dct_plan_ragged(None, 3, 2)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
+    arr = (ctypes.c_int * 2)(8, 0)
+    assert not L.fcc_dct_plan_ragged(arr, 2, 2)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
+
+
+def test_null_plan_calls():
+    L = binding.lib()
+    for f in (L.fcc_dct_forward, L.fcc_dct_inverse, L.fcc_dct_adjoint, L.fcc_dct_forward_host,
+              L.fcc_dct_inverse_host):
+        assert f(None, None, None, None) == binding.FCC_ERR_INVALID_ARG
+    assert L.fcc_dct_batch(None) == 0 and L.fcc_dct_points(None) == 0
+    L.fcc_dct_destroy(None)
+
+
+def test_describe_rejects_bad_order():
+    L = binding.lib()
+    n = ctypes.c_int64()
+    assert L.fcc_dct_describe(0, ctypes.byref(n), None, None, None, None, None, None, None, None, None) \
+        == binding.FCC_ERR_INVALID_ARG

@@ -1,0 +1,167 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over the whole output): FP64 dtypes 1e-12, FP32
+dtypes 1e-5 (the bar the FP32 transform must meet).  Element-wise maxima are
+reported in the assertion messages.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1807_10058_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"r64": 1e-12, "c64": 1e-12, "r32": 1e-5, "c32": 1e-5}
+RT = {"r64": np.float64, "c64": np.float64, "r32": np.float32, "c32": np.float32}
+CT = {"r64": np.complex128, "c64": np.complex128, "r32": np.complex64, "c32": np.complex64}
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(dtype).reshape(-1)).to(DEV)
+
+
+def host(t, shape):
+    return t.cpu().numpy().reshape(shape)
+
+
+def _input(dtype, n, batch, seed):
+    return inputs.uniform(n, batch, seed=seed, complex_=dtype.startswith("c"))
+
+
+@pytest.mark.parametrize("dtype", ["r64", "c64", "r32", "c32"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 10, 12])
+def test_small_orders_against_dense_definition(dtype, n):
+    batch = 3
+    x = _input(dtype, n, batch, seed=n)
+    y_ref = oracle.forward_dense(x, n)
+    g = inputs.uniform(n, batch, seed=100 + n, complex_=True)
+    a_ref = oracle.adjoint_dense(g, n)
+    real = dtype.startswith("r")
+    with binding.Plan(n, batch, dtype) as p:
+        xd = dev(x, RT[dtype] if real else CT[dtype])
+        y = host(p.forward(xd), x.shape)
+        xi = host(p.inverse(dev(y_ref, CT[dtype])), x.shape)
+        a = host(p.adjoint(dev(g, CT[dtype])), x.shape)
+    assert rel(y, y_ref) < TOL[dtype], (rel(y, y_ref), np.abs(y - y_ref).max())
+    assert rel(xi, x) < TOL[dtype] * 4, rel(xi, x)
+    a_want = a_ref.real if real else a_ref
+    assert rel(a, a_want) < TOL[dtype], rel(a, a_want)
+
+
+@pytest.mark.parametrize("dtype", ["r64", "r32", "c32"])
+@pytest.mark.parametrize("n", [16, 24, 40, 64])
+def test_medium_orders_full_volumes(dtype, n):
+    batch = 2
+    x = inputs.smoothed_noise(n, batch, seed=7) if dtype.startswith("r") else _input(dtype, n, batch, 3)
+    y_ref = oracle.forward_sum_fft(x, n)
+    real = dtype.startswith("r")
+    with binding.Plan(n, batch, dtype) as p:
+        y = host(p.forward(dev(x, RT[dtype] if real else CT[dtype])), x.shape)
+        xi = host(p.inverse(dev(y_ref, CT[dtype])), x.shape)
+        g = y_ref / np.linalg.norm(y_ref)
+        a = host(p.adjoint(dev(g, CT[dtype])), x.shape)
+    assert rel(y, y_ref) < TOL[dtype], rel(y, y_ref)
+    assert rel(xi, x) < TOL[dtype] * 4, rel(xi, x)
+    a_ref = oracle.adjoint_sum_fft(g, n)
+    assert rel(a, a_ref.real if real else a_ref) < TOL[dtype]
+
+
+def _full_size(n, batch, checked, seed, maker):
+    """Batch of `batch` volumes of order n on the device; the volumes listed
+    in `checked` come from the seeded host generator, the rest are device
+    noise of the same scale.  Returns (device tensor, {v: host volume})."""
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(seed)
+    x = torch.rand(batch * n ** 3, generator=gen, device=DEV, dtype=torch.float32) * 2 - 1
+    hv = {}
+    for v in checked:
+        vol = maker(n, 1, seed=seed + v)[0]
+        hv[v] = vol
+        x[v * n ** 3:(v + 1) * n ** 3] = torch.from_numpy(vol.astype(np.float32).reshape(-1)).to(DEV)
+    return x, hv
+
+
+@pytest.mark.parametrize("n,batch,maker", [(128, 64, inputs.phantom), (64, 256, inputs.smoothed_noise),
+                                           (96, 32, inputs.phantom)])
+def test_full_size_sampled_rows_and_round_trip(n, batch, maker):
+    checked = [0, batch // 2, batch - 1]
+    x, hv = _full_size(n, batch, checked, seed=11, maker=maker)
+    rng = np.random.default_rng(n)
+    with binding.Plan(n, batch, "r32") as p:
+        y = p.forward(x)
+        xr = p.inverse(y)
+        torch.cuda.synchronize()
+        # round trip on every volume (property at any size)
+        err_rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
+        assert err_rt < 1e-5, err_rt
+        for v in checked:
+            rows = np.concatenate([[0, n ** 3 - 1], rng.integers(0, n ** 3, size=6)])
+            ref = oracle.forward_rows(hv[v].astype(np.float32).astype(np.float64), n, rows)
+            got = y[v * n ** 3 + torch.from_numpy(rows).to(DEV)].cpu().numpy()
+            # sampled rows: compare against the scale of the whole output
+            scale = np.sqrt(np.mean(np.abs(y[v * n ** 3:(v + 1) * n ** 3].cpu().numpy()) ** 2))
+            assert np.abs(got - ref).max() / scale < 1e-5, (v, np.abs(got - ref).max() / scale)
+
+
+@pytest.mark.parametrize("dtype", ["r64", "r32"])
+def test_ragged_plan_matches_per_volume_oracle(dtype):
+    orders = [8, 5, 12, 8, 1, 16, 3]
+    vols = [inputs.uniform(n, 1, seed=i)[0] for i, n in enumerate(orders)]
+    flat = np.concatenate([v.reshape(-1) for v in vols])
+    with binding.Plan(orders=orders, dtype=dtype) as p:
+        y = p.forward(dev(flat, RT[dtype])).cpu().numpy()
+        back = p.inverse(p.forward(dev(flat, RT[dtype]))).cpu().numpy()
+    off = 0
+    for v, n in zip(vols, orders):
+        ref = oracle.forward_dense(v, n).reshape(-1) if n <= 12 else oracle.forward_sum_fft(v, n).reshape(-1)
+        assert rel(y[off:off + n ** 3], ref) < TOL[dtype]
+        assert rel(back[off:off + n ** 3], v) < TOL[dtype] * 4
+        off += n ** 3
+
+
+def test_host_buffer_entry_point_matches_device_call():
+    n, batch = 16, 4
+    x = inputs.smoothed_noise(n, batch, seed=2).astype(np.float32)
+    with binding.Plan(n, batch, "r32") as p:
+        yd = p.forward(dev(x, np.float32)).cpu()
+        xh = torch.from_numpy(x.reshape(-1)).pin_memory()
+        yh = torch.empty(batch * n ** 3, dtype=torch.complex64).pin_memory()
+        p.forward_host(xh, yh)
+        torch.cuda.synchronize()
+    assert torch.equal(yd, yh)
+
+
+def test_bad_device_arguments_are_rejected():
+    n = 8
+    L = binding.lib()
+    with binding.Plan(n, 2, "r32") as p:
+        x = torch.zeros(2 * n ** 3 + 8, device=DEV)
+        y = torch.zeros(2 * n ** 3, device=DEV, dtype=torch.complex64)
+        st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        mis = ctypes.c_void_p(x.data_ptr() + 4)
+        assert L.fcc_dct_forward(p.handle, mis, ctypes.c_void_p(y.data_ptr()), st) == binding.FCC_ERR_INVALID_ARG
+        # overlapping input and output
+        yy = torch.zeros(4 * n ** 3, device=DEV, dtype=torch.complex64)
+        assert L.fcc_dct_forward(p.handle, ctypes.c_void_p(yy.data_ptr()), ctypes.c_void_p(yy.data_ptr() + 16),
+                                 st) == binding.FCC_ERR_INVALID_ARG
+        assert L.fcc_dct_forward(p.handle, None, ctypes.c_void_p(y.data_ptr()), st) == binding.FCC_ERR_INVALID_ARG
+
+
+def test_unsupported_order_reports_status():
+    with pytest.raises(binding.FccError) as e:
+        binding.Plan(37, 1, "r32")
+    assert e.value.status == binding.FCC_ERR_UNSUPPORTED
+    with pytest.raises(binding.FccError) as e:
+        binding.Plan(8, 1, "r32_tf32x3")
+    assert e.value.status == binding.FCC_ERR_UNSUPPORTED

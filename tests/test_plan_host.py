@@ -1,0 +1,112 @@
+"""Host logic of the CUDA library, checked on the CPU.
+
+The library exports its orbit tables (fcc_dct_describe, no CUDA call).  Here
+the per-orbit algorithm the kernels run is replayed in numpy from those
+tables -- gather 24 slots, class core, row phase, scatter; then the 3-D DFT
+-- and compared with the oracle's plain definition.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_10058_gb300 import binding
+
+V = np.array([1, 0, 3])
+RNG = np.random.default_rng(5)
+
+
+def _tables(n):
+    d = binding.describe(n)
+    d["W"] = binding.weyl_group()
+    return d
+
+
+def _slots(d, n, o):
+    k = d["reps"][o]
+    c = d["cls"][o]
+    p = d["W"] @ k                           # (24, 3) unreduced slots
+    kap = p - n * d["wrap"][c]
+    assert kap.min() >= 0 and kap.max() < n
+    idx = (kap[:, 0] * n + kap[:, 1]) * n + kap[:, 2]
+    R = np.exp(2j * np.pi * np.mod(p @ V, 8 * n) / (8 * n))
+    canon = d["canon"][c] == np.arange(24)
+    return c, idx, R, canon
+
+
+def emulate(d, n, vol, mode):
+    N = n ** 3
+    vol = np.asarray(vol, dtype=np.complex128).reshape(N)
+    out = np.zeros(N, dtype=np.complex128)
+    if mode == "fwd":
+        src = vol
+    elif mode == "inv":
+        src = np.fft.fftn(vol.reshape(n, n, n)).reshape(N) / N
+    else:
+        src = np.fft.fftn(vol.reshape(n, n, n)).reshape(N)
+    for o in range(len(d["reps"])):
+        c, idx, R, canon = _slots(d, n, o)
+        if mode == "fwd":
+            z = R * (d["fwd"][c] @ src[idx])
+            out[idx[canon]] = z[canon]
+        else:
+            t = np.where(canon, np.conj(R) * src[idx], 0)
+            x = d[mode][c] @ t
+            out[idx[canon]] = x[canon]
+    if mode == "fwd":
+        out = np.fft.ifftn(out.reshape(n, n, n)).reshape(N) * N
+    return out.reshape(n, n, n)
+
+
+def test_library_group_equals_oracle_group():
+    a = {tuple(w.ravel()) for w in binding.weyl_group()}
+    b = {tuple(w.ravel()) for w in oracle.weyl_group()}
+    assert a == b and len(a) == 24
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 24])
+def test_orbits_partition_the_grid(n):
+    d = _tables(n)
+    seen = np.zeros(n ** 3, dtype=int)
+    for o in range(len(d["reps"])):
+        k = d["reps"][o]
+        assert k.min() >= 0 and k.sum() <= n            # closed alcove
+        c, idx, R, canon = _slots(d, n, o)
+        seen[idx[canon]] += 1
+        assert len(set(idx[canon])) == canon.sum() == len(set(idx))
+    assert (seen == 1).all()
+    if n <= 4:
+        # no free orbit: the open alcove is empty, or (n=4) its only point
+        # (1,1,1) is fixed by the rotation of the extended diagram
+        assert d["free_class"] == -1
+    else:
+        fc = d["free_class"]
+        assert fc == 0
+        core = d["fwd"][fc] * 24
+        assert np.allclose(np.abs(core), 1)               # 8th roots of unity
+        assert np.allclose(np.mod(np.angle(core) / (2 * np.pi / 8) + 0.5, 1), 0.5)
+        frac = (d["cls"] == fc).sum() * 24 / n ** 3
+        assert frac > (0.6 if n >= 16 else 0.1)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 9, 12])
+def test_emulated_forward_inverse_adjoint_match_oracle(n):
+    d = _tables(n)
+    x = RNG.standard_normal((n, n, n)) + 1j * RNG.standard_normal((n, n, n))
+    D = oracle.dct_matrix(n)
+    y = (D @ x.reshape(-1)).reshape(n, n, n)
+    assert np.abs(emulate(d, n, x, "fwd") - y).max() < 1e-11 * max(1, n ** 1.5)
+    assert np.abs(emulate(d, n, y, "inv") - x).max() < 1e-11 * max(1, n ** 1.5)
+    g = RNG.standard_normal((n, n, n)) + 1j * RNG.standard_normal((n, n, n))
+    ah = (D.conj().T @ g.reshape(-1)).reshape(n, n, n)
+    assert np.abs(emulate(d, n, g, "adj") - ah).max() < 1e-11 * max(1, n ** 1.5)
+
+
+def test_emulated_forward_order_24_sampled_rows():
+    n = 24
+    d = _tables(n)
+    x = RNG.standard_normal((n, n, n))
+    y = emulate(d, n, x, "fwd").reshape(-1)
+    rows = RNG.integers(0, n ** 3, size=12)
+    assert np.abs(y[rows] - oracle.forward_rows(x, n, rows)).max() < 1e-10
