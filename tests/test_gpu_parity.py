@@ -106,12 +106,20 @@ def test_full_size_sampled_rows_and_round_trip(n, batch, maker):
         err_rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
         assert err_rt < 1e-5, err_rt
         for v in checked:
-            rows = np.concatenate([[0, n ** 3 - 1], rng.integers(0, n ** 3, size=6)])
-            ref = oracle.forward_rows(hv[v].astype(np.float32).astype(np.float64), n, rows)
-            got = y[v * n ** 3 + torch.from_numpy(rows).to(DEV)].cpu().numpy()
-            # sampled rows: compare against the scale of the whole output
-            scale = np.sqrt(np.mean(np.abs(y[v * n ** 3:(v + 1) * n ** 3].cpu().numpy()) ** 2))
-            assert np.abs(got - ref).max() / scale < 1e-5, (v, np.abs(got - ref).max() / scale)
+            # uniform rows estimate the whole-output relative L2 without bias;
+            # the first and last point are checked element-wise as well
+            rows = rng.integers(0, n ** 3, size=24)
+            edge = np.array([0, n ** 3 - 1])
+            allrows = np.concatenate([rows, edge])
+            ref = oracle.forward_rows(hv[v].astype(np.float32).astype(np.float64), n, allrows)
+            got = y[v * n ** 3 + torch.from_numpy(allrows).to(DEV)].cpu().numpy()
+            rms = torch.sqrt(torch.mean(torch.abs(y[v * n ** 3:(v + 1) * n ** 3]) ** 2)).item()
+            err = np.abs(got - ref)
+            est = np.sqrt(np.mean(err[:24] ** 2)) / rms
+            assert est < 1e-5, (v, est)
+            # per element: FFT rounding is absolute (scale of the whole output)
+            # plus a relative part for the few very large (DC-like) entries
+            assert (err <= 1e-5 * rms + 1e-6 * np.abs(ref)).all(), (v, err / (rms + np.abs(ref)))
 
 
 @pytest.mark.parametrize("dtype", ["r64", "r32"])
