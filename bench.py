@@ -216,7 +216,8 @@ def main():
     torch.cuda.synchronize()
     kern = plan.profile_read()
     plan.profile(False)
-    algo_bytes = {"orbit_mix_fwd": 12, "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16}
+    algo_bytes = {"orbit_mix_fwd": 12, "mix_tiled_fwd": 12, "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16,
+                  "fft_slab": 16, "fft_pencil": 16}
     top = max(kern.items(), key=lambda kv: kv[1][0])
     top_name, (top_ms, top_cnt) = top
     per_launch_ms = top_ms / top_cnt

@@ -8,11 +8,14 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
 #include "fcc_dct.h"
+#include "fft_fast.cuh"
 #include "kernels.cuh"
+#include "mix_tiled.cuh"
 #include "plan.h"
 
 using namespace fcc;
@@ -42,7 +45,17 @@ struct OrderTables {
     void* mat[3] = {nullptr, nullptr, nullptr};  // fwd, inv, adj
     void* phase = nullptr;                        // [8n] complex
     void* tw = nullptr;                           // [n] complex, exp(+2 pi i j / n)
+    // tiled mixing (FP32 plans)
+    int free_class = -1;
+    int ntiles = 0;
+    int32_t* tile_off = nullptr;
+    uint32_t* tile_reps = nullptr;
+    uint8_t* tile_cls = nullptr;
+    uint16_t* tile_pb = nullptr;
+    uint16_t* tile_pc = nullptr;
 };
+
+constexpr int kMaxStreams = 4;
 
 }  // namespace
 
@@ -60,6 +73,13 @@ struct fcc_plan {
     void* host_in_dev = nullptr;     // device staging for the *_host entry points
     void* host_out_dev = nullptr;
     std::vector<void*> allocs;
+    // chunked schedule: volumes per chunk and internal streams (fork / join
+    // with the caller's stream through events)
+    int64_t chunk_bytes = 32ll << 20;
+    int nstreams = 2;
+    cudaStream_t streams[kMaxStreams] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxStreams] = {};
     // per-kernel timing (fcc_dct_profile_enable)
     bool profiling = false;
     struct Rec { const char* name; cudaEvent_t a, b; };
@@ -140,6 +160,24 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     if ((s = upload(p, &t.phase, ph.data(), ph.size() * sizeof(T)))) return s;
     auto twv = to_pairs<T>(tw);
     if ((s = upload(p, &t.tw, twv.data(), twv.size() * sizeof(T)))) return s;
+    t.free_class = hp.free_class;
+    t.ntiles = (int)hp.tile_off.size() - 1;
+    if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
+    if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
+    if ((s = upload(p, (void**)&t.tile_cls, hp.tile_cls.data(), hp.tile_cls.size()))) return s;
+    if ((s = upload(p, (void**)&t.tile_pb, hp.tile_perm_b.data(), hp.tile_perm_b.size() * 2))) return s;
+    if ((s = upload(p, (void**)&t.tile_pc, hp.tile_perm_c.data(), hp.tile_perm_c.size() * 2))) return s;
+    if (sizeof(T) == 4 && hp.free_class >= 0) {
+        // the free-orbit cores do not depend on n: one constant copy per device
+        std::vector<float2> core(3 * 576);
+        const OrbitClass& oc = hp.classes[hp.free_class];
+        for (int e = 0; e < 576; ++e) {
+            core[e] = make_float2((float)oc.fwd[e].real(), (float)oc.fwd[e].imag());
+            core[576 + e] = make_float2((float)oc.inv[e].real(), (float)oc.inv[e].imag());
+            core[1152 + e] = make_float2((float)oc.adj[e].real(), (float)oc.adj[e].imag());
+        }
+        if (cudaMemcpyToSymbol(c_core, core.data(), core.size() * sizeof(float2)) != cudaSuccess) return FCC_ERR_CUDA;
+    }
     return FCC_OK;
 }
 
@@ -147,6 +185,9 @@ fcc_status upload_group() {
     const WeylGroup& G = weyl();
     if (cudaMemcpyToSymbol(c_W, G.m, sizeof(G.m)) != cudaSuccess) return FCC_ERR_CUDA;
     if (cudaMemcpyToSymbol(c_u, G.u, sizeof(G.u)) != cudaSuccess) return FCC_ERR_CUDA;
+    int dir[24];
+    slot_directions(dir);
+    if (cudaMemcpyToSymbol(c_dir, dir, sizeof(dir)) != cudaSuccess) return FCC_ERR_CUDA;
     return FCC_OK;
 }
 
@@ -157,6 +198,11 @@ void release(fcc_plan* p) {
     cudaSetDevice(p->device);
     for (void* a : p->allocs) cudaFree(a);
     for (auto& r : p->recs) { if (r.a) cudaEventDestroy(r.a); if (r.b) cudaEventDestroy(r.b); }
+    for (int i = 0; i < kMaxStreams; ++i) {
+        if (p->streams[i]) cudaStreamDestroy(p->streams[i]);
+        if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
+    }
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     for (auto e : p->event_pool) cudaEventDestroy(e);
     cudaSetDevice(cur);
     delete p;
@@ -193,12 +239,22 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         p->tabs[n] = t;
     }
     if (s == FCC_OK) {
-        // workspace: enough whole volumes for ~64 MB, at least one volume
+        if (const char* e = std::getenv("FCC_CHUNK_MB")) p->chunk_bytes = std::max(1, std::atoi(e)) * (1ll << 20);
+        if (const char* e = std::getenv("FCC_STREAMS")) p->nstreams = std::min(kMaxStreams, std::max(1, std::atoi(e)));
+        for (int i = 0; i < p->nstreams && s == FCC_OK; ++i) {
+            if (cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+                s = FCC_ERR_CUDA;
+        }
+        if (s == FCC_OK && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
+    }
+    if (s == FCC_OK) {
+        // workspace for inverse / adjoint: one chunk per internal stream
         const int64_t bytes_per_pt = 2 * real_size(dtype);
-        int64_t chunk_pts = std::max<int64_t>(maxpts, (int64_t(64) << 20) / bytes_per_pt);
+        int64_t chunk_pts = std::max<int64_t>(maxpts, p->chunk_bytes / bytes_per_pt);
         chunk_pts = std::min<int64_t>(chunk_pts, p->points);
         p->scratch_points = chunk_pts;
-        s = dev_alloc(p, &p->scratch, chunk_pts * bytes_per_pt);
+        s = dev_alloc(p, &p->scratch, chunk_pts * bytes_per_pt * p->nstreams);
     }
     if (s != FCC_OK) {
         release(p);
@@ -313,10 +369,174 @@ fcc_status launch_mix(const OrderTables& t, int mode, bool real_in, bool real_ou
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
+// --- FP32 fast path -------------------------------------------------------
+
+template <int N>
+fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out, int64_t nvol, const float2* tw,
+                             cudaStream_t st) {
+    using L = FastLayout<N>;
+    if (slab) {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(fft_slab_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
+            cudaFuncSetAttribute(fft_slab_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
+            attr = true;
+        }
+        ProfScope ps("fft_slab", st);
+        const unsigned grid = (unsigned)(nvol * N);
+        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kFastThreads, L::slab_smem, st>>>(in, out, tw);
+        else fft_slab_kernel<N, -1><<<grid, kFastThreads, L::slab_smem, st>>>(in, out, tw);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(fft_pencil_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+            cudaFuncSetAttribute(fft_pencil_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+            attr = true;
+        }
+        constexpr int CPB = kFastWarps * L::PPW;
+        const unsigned grid = (unsigned)(nvol * N * ((N + CPB - 1) / CPB));
+        ProfScope ps("fft_pencil", st);
+        if (sign > 0) fft_pencil_kernel<N, 1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw);
+        else fft_pencil_kernel<N, -1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw);
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
+bool has_fast_fft(int n) {
+    switch (n) {
+        case 128: case 96: case 64: case 32: case 16: return true;
+        default: return false;
+    }
+}
+
+fcc_status launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
+                           const float2* tw, cudaStream_t st) {
+    switch (n) {
+        case 128: return launch_fast_fft_n<128>(slab, sign, in, out, nvol, tw, st);
+        case 96: return launch_fast_fft_n<96>(slab, sign, in, out, nvol, tw, st);
+        case 64: return launch_fast_fft_n<64>(slab, sign, in, out, nvol, tw, st);
+        case 32: return launch_fast_fft_n<32>(slab, sign, in, out, nvol, tw, st);
+        case 16: return launch_fast_fft_n<16>(slab, sign, in, out, nvol, tw, st);
+        default: return FCC_ERR_UNSUPPORTED;
+    }
+}
+
+fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
+                            float* out, int64_t nvol, float scale, cudaStream_t st) {
+    TiledMixArgs a;
+    a.tile_off = t.tile_off;
+    a.reps = t.tile_reps;
+    a.cls = t.tile_cls;
+    a.permb = t.tile_pb;
+    a.permc = t.tile_pc;
+    a.mats = (const float*)t.mat[mode];
+    a.wrap = t.wrap;
+    a.canon_mask = t.canon_mask;
+    a.phase = (const float2*)t.phase;
+    a.n = t.n;
+    a.free_class = t.free_class;
+    a.n3 = (int64_t)t.n * t.n * t.n;
+    a.scale = scale;
+    const size_t smem = mix_tiled_smem(t.n);
+    static bool attr = false;
+    if (!attr) {
+        const int lim = 200 * 1024;
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        attr = true;
+    }
+    static const char* names[3] = {"mix_tiled_fwd", "mix_tiled_inv", "mix_tiled_adj"};
+    for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
+        const int64_t nv = std::min<int64_t>(65535, nvol - v0);
+        dim3 grid((unsigned)t.ntiles, (unsigned)nv);
+        const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
+        float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
+        ProfScope ps(names[mode], st);
+        if (mode == MODE_FWD) {
+            if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+        } else if (mode == MODE_INV) {
+            if (real_out) mix_tiled_kernel<MODE_INV, false, true><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            else mix_tiled_kernel<MODE_INV, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+        } else {
+            if (real_out) mix_tiled_kernel<MODE_ADJ, false, true><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            else mix_tiled_kernel<MODE_ADJ, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
+// 3-D DFT of nvol complex volumes: fast slab + pencil passes when the order
+// has a register factorisation, else the generic pass per axis.
+fcc_status launch_dft3(const OrderTables& t, int sign, const float* in, float* out, int64_t nvol, cudaStream_t st) {
+    if (has_fast_fft(t.n)) {
+        const float2* tw = (const float2*)t.tw;
+        fcc_status s;
+        if (sign > 0) {
+            if ((s = launch_fast_fft(t.n, true, sign, (const float2*)in, (float2*)out, nvol, tw, st))) return s;
+            return launch_fast_fft(t.n, false, sign, (const float2*)out, (float2*)out, nvol, tw, st);
+        }
+        if ((s = launch_fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, st))) return s;
+        return launch_fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, st);
+    }
+    fcc_status s = launch_fft<float>(t, in, out, nvol, 0, sign, st);
+    if (!s) s = launch_fft<float>(t, out, out, nvol, 1, sign, st);
+    if (!s) s = launch_fft<float>(t, out, out, nvol, 2, sign, st);
+    return s;
+}
+
+int64_t chunk_vols(const fcc_plan* p, int n) {
+    const int64_t n3 = (int64_t)n * n * n;
+    return std::max<int64_t>(1, p->chunk_bytes / (n3 * 8));
+}
+
+// FP32: chunks of volumes round-robin over the internal streams so that each
+// chunk's complex intermediate stays in L2 between its passes.
+fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const float* in, float* out, int64_t nvol,
+                          cudaStream_t st) {
+    const bool rin = is_real_in(p->dtype);
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    const int64_t cv = std::min<int64_t>(chunk_vols(p, t.n), std::max<int64_t>(1, p->scratch_points / n3));
+    const int ns = p->nstreams;
+    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    fcc_status s = FCC_OK;
+    int c = 0;
+    for (int64_t v0 = 0; v0 < nvol && !s; v0 += cv, ++c) {
+        const int64_t nv = std::min(cv, nvol - v0);
+        cudaStream_t ss = p->streams[c % ns];
+        if (which == 0) {
+            const float* x = in + v0 * n3 * (rin ? 1 : 2);
+            float* y = out + v0 * n3 * 2;
+            s = launch_mix_tiled(t, MODE_FWD, rin, false, x, y, nv, 1.f, ss);
+            if (!s) s = launch_dft3(t, +1, y, y, nv, ss);
+        } else {
+            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            const float* y = in + v0 * n3 * 2;
+            float* x = out + v0 * n3 * (rin ? 1 : 2);
+            s = launch_dft3(t, -1, y, ws, nv, ss);
+            const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
+            if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, rin, ws, x, nv, scale, ss);
+        }
+    }
+    for (int i = 0; i < ns; ++i) {
+        if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    return s;
+}
+
 // Run a group of `nvol` consecutive volumes of the same order.
 template <typename T>
 fcc_status run_group(fcc_plan* p, int which, const OrderTables& t, const T* in, T* out, int64_t nvol,
                      cudaStream_t st) {
+    if (sizeof(T) == 4 && t.n > 1)
+        return run_group_fast(p, which, t, (const float*)in, (float*)out, nvol, st);
     const bool rin = is_real_in(p->dtype);
     const int64_t n3 = (int64_t)t.n * t.n * t.n;
     fcc_status s = FCC_OK;
@@ -442,7 +662,11 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         const int64_t n3 = (int64_t)n * n * n;
         const int64_t nv = e - v;
         const int mix = (int)((nv + 65534) / 65535);
-        if (which == 0) total += mix + 3;
+        if (!is_double(p->dtype) && n > 1) {
+            const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
+            const int64_t chunks = (nv + cv - 1) / cv;
+            total += (int)(chunks * (1 + (has_fast_fft(n) ? 2 : 3)));
+        } else if (which == 0) total += mix + 3;
         else {
             const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
             total += (int)((nv + chunk - 1) / chunk) * 4;

@@ -1,0 +1,192 @@
+// Fast 3-D DFT passes for orders with a register-resident factorisation
+// n = R1 * G (G threads per pencil, R1 values per thread):
+//
+//   fft_slab_kernel    DFT along the two fast axes of one n x n slab:
+//                      rows straight from global memory into registers,
+//                      columns from a padded shared-memory copy of the slab.
+//   fft_pencil_kernel  DFT along the slow axis, 32/G pencils per warp,
+//                      straight from and back to global memory.
+//
+// Within a pencil: a = j + G m (j = thread, m < R1); step 1 is a length-R1
+// DFT over m in registers, then the twiddle exp(S 2 pi i j k2 / n), then an
+// exchange through a small per-warp buffer (__syncwarp only) and a length-G
+// DFT over j, giving X[k2 + R1 k1].  Every global access of a warp touches
+// whole 32-byte sectors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dft_reg.cuh"
+
+namespace fcc {
+
+template <int N> struct FftShape { static constexpr bool ok = false; static constexpr int R1 = 1, G = 1; };
+#define FCC_SHAPE(NN, RR, GG) \
+    template <> struct FftShape<NN> { static constexpr bool ok = true; static constexpr int R1 = RR, G = GG; };
+FCC_SHAPE(128, 16, 8)
+FCC_SHAPE(96, 24, 4)
+FCC_SHAPE(64, 8, 8)
+FCC_SHAPE(32, 8, 4)
+FCC_SHAPE(16, 4, 4)
+#undef FCC_SHAPE
+
+constexpr int kFastThreads = 256;
+constexpr int kFastWarps = kFastThreads / 32;
+
+template <int N>
+struct FastLayout {
+    static constexpr int R1 = FftShape<N>::R1;
+    static constexpr int G = FftShape<N>::G;
+    static constexpr int PPW = 32 / G;                 // pencils per warp
+    static constexpr int LD = N + 4;                   // slab row stride (complex)
+    static constexpr int EXP = G * (R1 + 1);           // exchange stride per pencil
+    static constexpr int EXW = PPW * EXP;              // exchange per warp
+    static constexpr size_t slab_smem = (size_t)(N * LD + kFastWarps * EXW + N) * sizeof(float2);
+    static constexpr size_t pencil_smem = (size_t)(kFastWarps * EXW + N) * sizeof(float2);
+};
+
+// One pencil step for the thread holding v[m] = x[j + G m]: DFT over m,
+// twiddle, exchange, DFT over j.  On return the thread owns outputs
+// X[k2 + R1 k1] for k2 = q + G e (e < R1/G... handled by the caller via emit).
+template <int N, int S>
+struct PencilFft {
+    using L = FastLayout<N>;
+    static constexpr int R1 = L::R1, G = L::G;
+    static_assert(R1 % G == 0, "R1 must be a multiple of G");
+
+    // ex: this pencil's exchange area (G * (R1+1) complex); tw: exp(+2 pi i m / N)
+    template <typename Emit>
+    __device__ __forceinline__ static void run(float (&vr)[R1], float (&vi)[R1], int j, float2* ex,
+                                               const float2* tw, Emit emit) {
+        reg::Dft<R1, S, float>::run(vr, vi);
+#pragma unroll
+        for (int k2 = 1; k2 < R1; ++k2) {
+            const float2 w = tw[(j * k2) % N];
+            const float wi = S > 0 ? w.y : -w.y;
+            const float t = vr[k2] * w.x - vi[k2] * wi;
+            vi[k2] = vr[k2] * wi + vi[k2] * w.x;
+            vr[k2] = t;
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < R1; ++k2) ex[j * (R1 + 1) + k2] = make_float2(vr[k2], vi[k2]);
+        __syncwarp();
+        const int q = j;
+#pragma unroll
+        for (int e = 0; e < R1 / G; ++e) {
+            const int k2 = q + G * e;
+            float ur[G], ui[G];
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj) {
+                const float2 t = ex[jj * (R1 + 1) + k2];
+                ur[jj] = t.x;
+                ui[jj] = t.y;
+            }
+            reg::Dft<G, S, float>::run(ur, ui);
+#pragma unroll
+            for (int k1 = 0; k1 < G; ++k1) emit(k2 + R1 * k1, ur[k1], ui[k1]);
+        }
+        __syncwarp();
+    }
+};
+
+// grid.x = number of slabs (volumes * N); in and out may alias.
+template <int N, int S>
+__global__ void __launch_bounds__(kFastThreads, 1)
+fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
+    using L = FastLayout<N>;
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* slab = reinterpret_cast<float2*>(smem_raw);
+    float2* exall = slab + N * LD;
+    float2* tw = exall + kFastWarps * L::EXW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * N * N;
+
+    // rows (fastest axis)
+    {
+        const int p = lane / G, j = lane % G;
+        float2* ex = exall + warp * L::EXW + p * L::EXP;
+        for (int r0 = 0; r0 < N; r0 += kFastWarps * PPW) {
+            const int r = r0 + warp * PPW + p;
+            const bool act = r < N;   // warp-uniform: N is a multiple of PPW
+            if (act) {
+                float vr[R1], vi[R1];
+                const float2* src = in + base + (int64_t)r * N + j;
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = src[G * m];
+                    vr[m] = t.x;
+                    vi[m] = t.y;
+                }
+                float2* row = slab + r * LD;
+                PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int c, float xr, float xi) {
+                    row[c] = make_float2(xr, xi);
+                });
+            }
+        }
+    }
+    __syncthreads();
+    // columns (middle axis), results straight to global memory
+    {
+        const int cl = lane % PPW, j = lane / PPW;
+        float2* ex = exall + warp * L::EXW + cl * L::EXP;
+        for (int c0 = 0; c0 < N; c0 += kFastWarps * PPW) {
+            const int c = c0 + warp * PPW + cl;
+            if (c0 + warp * PPW < N) {
+                float vr[R1], vi[R1];
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = slab[(j + G * m) * LD + c];
+                    vr[m] = t.x;
+                    vi[m] = t.y;
+                }
+                float2* dst = out + base + c;
+                PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int b, float xr, float xi) {
+                    dst[(int64_t)b * N] = make_float2(xr, xi);
+                });
+            }
+        }
+    }
+}
+
+// grid.x = volumes * N (b) * ceil(N / CPB) column blocks; pencils along the
+// slowest axis.  in and out may alias.
+template <int N, int S>
+__global__ void __launch_bounds__(kFastThreads)
+fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
+    using L = FastLayout<N>;
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW;
+    constexpr int CPB = kFastWarps * PPW;
+    constexpr int CBLK = (N + CPB - 1) / CPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* exall = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = exall + kFastWarps * L::EXW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    __syncthreads();
+    const int64_t blk = blockIdx.x;
+    const int64_t vol = blk / ((int64_t)N * CBLK);
+    const int rem = (int)(blk - vol * N * CBLK);
+    const int b = rem / CBLK;
+    const int cb = rem % CBLK;
+    const int cl = lane % PPW, j = lane / PPW;
+    const int c = cb * CPB + warp * PPW + cl;
+    if (cb * CPB + warp * PPW >= N) return;   // warp-uniform
+    float2* ex = exall + warp * L::EXW + cl * L::EXP;
+    const int64_t NN = (int64_t)N * N;
+    const int64_t base = vol * NN * N + (int64_t)b * N + c;
+    float vr[R1], vi[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+        const float2 t = in[base + (int64_t)(j + G * m) * NN];
+        vr[m] = t.x;
+        vi[m] = t.y;
+    }
+    PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int a, float xr, float xi) {
+        out[base + (int64_t)a * NN] = make_float2(xr, xi);
+    });
+}
+
+}  // namespace fcc

@@ -266,7 +266,74 @@ int build_host_plan(int n, HostPlan& P) {
         P.cls[at] = (uint8_t)r;
     }
     for (int c = 0; c < ncls; ++c) P.orbits_per_class_max = std::max(P.orbits_per_class_max, P.class_count[c]);
+
+    // Tiles.
+    struct Item { int64_t key; int a, b, c; uint32_t rep; uint8_t cls; };
+    std::vector<Item> items(P.reps.size());
+    const int nta = n / kTileA + 1, ntb = n / kTileB + 1, ntc = n / kTileC + 1;
+    for (size_t o = 0; o < P.reps.size(); ++o) {
+        const int k1 = P.reps[o] & 1023, k2 = (P.reps[o] >> 10) & 1023, k3 = (P.reps[o] >> 20) & 1023;
+        const int a = k1 + k2 + k3, b = k1 + k2, c = k1;
+        const int64_t tk = ((int64_t)(a / kTileA) * ntb + b / kTileB) * ntc + c / kTileC;
+        // a' fastest inside the tile
+        const int64_t local = ((int64_t)(c % kTileC) * kTileB + b % kTileB) * kTileA + a % kTileA;
+        items[o] = {tk * kTileMax + local, a, b, c, P.reps[o], P.cls[o]};
+    }
+    (void)nta;
+    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.key < y.key; });
+    P.tile_off.clear();
+    P.tile_reps.resize(items.size());
+    P.tile_cls.resize(items.size());
+    P.tile_perm_b.resize(items.size());
+    P.tile_perm_c.resize(items.size());
+    size_t i = 0;
+    while (i < items.size()) {
+        size_t e = i;
+        const int64_t tk = items[i].key / kTileMax;
+        while (e < items.size() && items[e].key / kTileMax == tk) ++e;
+        P.tile_off.push_back((int32_t)i);
+        P.max_tile = std::max(P.max_tile, (int)(e - i));
+        std::vector<int> ord(e - i);
+        for (size_t t = i; t < e; ++t) {
+            P.tile_reps[t] = items[t].rep;
+            P.tile_cls[t] = items[t].cls;
+            ord[t - i] = (int)(t - i);
+        }
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+            const Item& X = items[i + x];
+            const Item& Y = items[i + y];
+            if (X.a != Y.a) return X.a < Y.a;
+            if (X.c != Y.c) return X.c < Y.c;
+            return X.b < Y.b;
+        });
+        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_b[i + t] = (uint16_t)ord[t];
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+            const Item& X = items[i + x];
+            const Item& Y = items[i + y];
+            if (X.a != Y.a) return X.a < Y.a;
+            if (X.b != Y.b) return X.b < Y.b;
+            return X.c < Y.c;
+        });
+        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_c[i + t] = (uint16_t)ord[t];
+        i = e;
+    }
+    P.tile_off.push_back((int32_t)items.size());
     return 0;
+}
+
+void slot_directions(int dir[24]) {
+    const WeylGroup& G = weyl();
+    // d1 = e3 (a'), d2 = (0,1,-1) (b'), d3 = (1,-1,0) (c')
+    const int d[3][3] = {{0, 0, 1}, {0, 1, -1}, {1, -1, 0}};
+    for (int g = 0; g < 24; ++g) {
+        dir[g] = 3;
+        for (int i = 0; i < 3; ++i) {
+            int img[3];
+            for (int r = 0; r < 3; ++r)
+                img[r] = G.m[g][3 * r] * d[i][0] + G.m[g][3 * r + 1] * d[i][1] + G.m[g][3 * r + 2] * d[i][2];
+            if (img[0] == 0 && img[1] == 0 && img[2] == 1) dir[g] = i;
+        }
+    }
 }
 
 }  // namespace fcc

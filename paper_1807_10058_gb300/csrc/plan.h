@@ -66,7 +66,29 @@ struct HostPlan {
     int64_t orbits_per_class_max = 0;
     std::vector<int64_t> class_begin;  // orbits are sorted by class; [begin, begin+count)
     std::vector<int64_t> class_count;
+
+    // Tiles for the locality-aware mixing kernel.  With
+    //   a' = k1 + k2 + k3, b' = k1 + k2, c' = k1
+    // the representative is k = a' e3 + b' (0,1,-1) + c' (1,-1,0) and the
+    // closed alcove is n >= a' >= b' >= c' >= 0.  Representatives are grouped
+    // into boxes of kTileA x kTileB x kTileC in (a', b', c'); within a tile
+    // they are listed with a' fastest (then b', then c').  perm_b / perm_c list
+    // the same tile with b' (resp. c') fastest, as indices into that order.
+    std::vector<int32_t> tile_off;   // [ntiles + 1], offsets into tile_reps
+    std::vector<uint32_t> tile_reps; // packed representatives, tile order
+    std::vector<uint8_t> tile_cls;
+    std::vector<uint16_t> tile_perm_b;
+    std::vector<uint16_t> tile_perm_c;
+    int max_tile = 0;
 };
+
+constexpr int kTileA = 8, kTileB = 8, kTileC = 4;
+constexpr int kTileMax = kTileA * kTileB * kTileC;
+
+// For slot g, the direction in (a', b', c') along which consecutive
+// representatives map to consecutive memory: 0 = a', 1 = b', 2 = c',
+// 3 = none of the three (the fourth direction -e1).
+void slot_directions(int dir[24]);
 
 // Orders supported by the packing of representatives.
 constexpr int kMaxOrder = 512;

@@ -1,0 +1,49 @@
+"""Differentiation through the C ABI: the backward pass is the adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1807_10058_gb300 import binding, inputs
+from paper_1807_10058_gb300.autograd import fcc_dct
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.mark.parametrize("dtype,n", [("r64", 4), ("c64", 3), ("r64", 8)])
+def test_gradcheck_fp64(dtype, n):
+    real = dtype == "r64"
+    with binding.Plan(n, 2, dtype) as p:
+        t = torch.float64 if real else torch.complex128
+        x = torch.randn(2 * n ** 3, dtype=t, device=DEV, requires_grad=True)
+        assert torch.autograd.gradcheck(lambda v: fcc_dct(v, p), (x,), eps=1e-6, atol=1e-7, rtol=1e-7)
+
+
+def test_masked_reconstruction_gradient_matches_oracle():
+    """L = ||M . (D x) - b||^2, grad = 2 Re D^H (M . (M . D x - b))."""
+    n, batch = 8, 2
+    x0 = inputs.phantom(n, batch, seed=3)
+    xt = inputs.phantom(n, batch, seed=9)
+    M = inputs.bernoulli_mask(n, batch, seed=4, p=0.1).astype(np.float64)
+    b = M * oracle.forward_dense(xt, n)
+    with binding.Plan(n, batch, "r64") as p:
+        x = torch.from_numpy(x0.reshape(-1)).to(DEV).requires_grad_(True)
+        Mt = torch.from_numpy(M.reshape(-1)).to(DEV)
+        bt = torch.from_numpy(b.reshape(-1)).to(DEV)
+        L = torch.sum(torch.abs(Mt * fcc_dct(x, p) - bt) ** 2)
+        L.backward()
+        g = x.grad.cpu().numpy().reshape(x0.shape)
+    r = M * (M * oracle.forward_dense(x0, n) - b)
+    ref = 2 * oracle.adjoint_dense(r, n).real
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_adjoint_dot_product_fp32_large():
+    n, batch = 64, 2
+    with binding.Plan(n, batch, "r32") as p:
+        x = torch.randn(batch * n ** 3, device=DEV)
+        g = torch.randn(batch * n ** 3, device=DEV, dtype=torch.complex64)
+        lhs = torch.sum((torch.conj(g) * p.forward(x)).real.double())
+        rhs = torch.sum((x * p.adjoint(g)).double())
+        assert abs(lhs - rhs) / abs(lhs) < 1e-5
