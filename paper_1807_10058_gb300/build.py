@@ -39,7 +39,7 @@ def build(force=False, verbose=False):
         if os.path.getmtime(LIB) >= newest:
             return LIB
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+    common = ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")

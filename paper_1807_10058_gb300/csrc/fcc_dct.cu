@@ -51,8 +51,8 @@ struct OrderTables {
     int32_t* tile_off = nullptr;
     uint32_t* tile_reps = nullptr;
     uint8_t* tile_cls = nullptr;
-    uint16_t* tile_pb = nullptr;
-    uint16_t* tile_pc = nullptr;
+    uint8_t* tile_pb = nullptr;
+    uint8_t* tile_pc = nullptr;
 };
 
 constexpr int kMaxStreams = 4;
@@ -165,8 +165,14 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_cls, hp.tile_cls.data(), hp.tile_cls.size()))) return s;
-    if ((s = upload(p, (void**)&t.tile_pb, hp.tile_perm_b.data(), hp.tile_perm_b.size() * 2))) return s;
-    if ((s = upload(p, (void**)&t.tile_pc, hp.tile_perm_c.data(), hp.tile_perm_c.size() * 2))) return s;
+    if ((s = upload(p, (void**)&t.tile_pb, hp.tile_perm_b.data(), hp.tile_perm_b.size()))) return s;
+    if ((s = upload(p, (void**)&t.tile_pc, hp.tile_perm_c.data(), hp.tile_perm_c.size()))) return s;
+    if (hp.free_class >= 0) {
+        // the kernels hard-wire the free-orbit wrap vectors
+        for (int g = 0; g < 24; ++g)
+            for (int i = 0; i < 3; ++i)
+                if (hp.classes[hp.free_class].wrap[g][i] != wc::K::t.fw[g][i]) return FCC_ERR_UNSUPPORTED;
+    }
     if (sizeof(T) == 4 && hp.free_class >= 0) {
         // the free-orbit cores do not depend on n: one constant copy per device
         std::vector<float2> core(3 * 576);
@@ -183,11 +189,16 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
 
 fcc_status upload_group() {
     const WeylGroup& G = weyl();
+    // the kernels' compile-time copy of W must match the plan builder's
+    for (int g = 0; g < 24; ++g)
+        for (int i = 0; i < 9; ++i)
+            if (wc::K::t.m[g][i] != G.m[g][i]) return FCC_ERR_UNSUPPORTED;
     if (cudaMemcpyToSymbol(c_W, G.m, sizeof(G.m)) != cudaSuccess) return FCC_ERR_CUDA;
     if (cudaMemcpyToSymbol(c_u, G.u, sizeof(G.u)) != cudaSuccess) return FCC_ERR_CUDA;
     int dir[24];
     slot_directions(dir);
-    if (cudaMemcpyToSymbol(c_dir, dir, sizeof(dir)) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int g = 0; g < 24; ++g)
+        if (dir[g] != wc::K::t.dir[g]) return FCC_ERR_UNSUPPORTED;
     return FCC_OK;
 }
 
@@ -384,8 +395,8 @@ fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out,
         }
         ProfScope ps("fft_slab", st);
         const unsigned grid = (unsigned)(nvol * N);
-        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kFastThreads, L::slab_smem, st>>>(in, out, tw);
-        else fft_slab_kernel<N, -1><<<grid, kFastThreads, L::slab_smem, st>>>(in, out, tw);
+        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw);
+        else fft_slab_kernel<N, -1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -393,7 +404,7 @@ fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out,
             cudaFuncSetAttribute(fft_pencil_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
             attr = true;
         }
-        constexpr int CPB = kFastWarps * L::PPW;
+        constexpr int CPB = kFastWarps * L::PPW * 2;
         const unsigned grid = (unsigned)(nvol * N * ((N + CPB - 1) / CPB));
         ProfScope ps("fft_pencil", st);
         if (sign > 0) fft_pencil_kernel<N, 1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw);
@@ -434,9 +445,19 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
     a.canon_mask = t.canon_mask;
     a.phase = (const float2*)t.phase;
     a.n = t.n;
+    {
+        const int n = t.n;
+        for (int g = 0; g < 24; ++g) {
+            for (int j = 0; j < 3; ++j)
+                a.lin[g][j] = wc::K::t.m[g][j] * n * n + wc::K::t.m[g][3 + j] * n + wc::K::t.m[g][6 + j];
+            a.lin[g][3] = -n * (wc::K::t.fw[g][0] * n * n + wc::K::t.fw[g][1] * n + wc::K::t.fw[g][2]);
+        }
+    }
+    a.ncls = t.n_classes;
     a.free_class = t.free_class;
     a.n3 = (int64_t)t.n * t.n * t.n;
     a.scale = scale;
+    if (t.n_classes > kMaxClasses) return FCC_ERR_UNSUPPORTED;
     const size_t smem = mix_tiled_smem(t.n);
     static bool attr = false;
     if (!attr) {
@@ -452,19 +473,20 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
     static const char* names[3] = {"mix_tiled_fwd", "mix_tiled_inv", "mix_tiled_adj"};
     for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
         const int64_t nv = std::min<int64_t>(65535, nvol - v0);
-        dim3 grid((unsigned)t.ntiles, (unsigned)nv);
+        dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
         const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
         float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
+        const int nt = t.ntiles;
         ProfScope ps(names[mode], st);
         if (mode == MODE_FWD) {
-            if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
-            else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
         } else if (mode == MODE_INV) {
-            if (real_out) mix_tiled_kernel<MODE_INV, false, true><<<grid, kTileMax, smem, st>>>(src, dst, a);
-            else mix_tiled_kernel<MODE_INV, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            if (real_out) mix_tiled_kernel<MODE_INV, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            else mix_tiled_kernel<MODE_INV, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
         } else {
-            if (real_out) mix_tiled_kernel<MODE_ADJ, false, true><<<grid, kTileMax, smem, st>>>(src, dst, a);
-            else mix_tiled_kernel<MODE_ADJ, false, false><<<grid, kTileMax, smem, st>>>(src, dst, a);
+            if (real_out) mix_tiled_kernel<MODE_ADJ, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            else mix_tiled_kernel<MODE_ADJ, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
         }
     }
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;

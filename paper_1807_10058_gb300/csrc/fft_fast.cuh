@@ -30,8 +30,10 @@ FCC_SHAPE(32, 8, 4)
 FCC_SHAPE(16, 4, 4)
 #undef FCC_SHAPE
 
-constexpr int kFastThreads = 256;
+constexpr int kFastThreads = 256;            // pencil kernel
 constexpr int kFastWarps = kFastThreads / 32;
+constexpr int kSlabThreads = 512;            // slab kernel: one block per SM, 16 warps
+constexpr int kSlabWarps = kSlabThreads / 32;
 
 template <int N>
 struct FastLayout {
@@ -41,7 +43,7 @@ struct FastLayout {
     static constexpr int LD = N + 4;                   // slab row stride (complex)
     static constexpr int EXP = G * (R1 + 1);           // exchange stride per pencil
     static constexpr int EXW = PPW * EXP;              // exchange per warp
-    static constexpr size_t slab_smem = (size_t)(N * LD + kFastWarps * EXW + N) * sizeof(float2);
+    static constexpr size_t slab_smem = (size_t)(N * LD + kSlabWarps * EXW + N) * sizeof(float2);
     static constexpr size_t pencil_smem = (size_t)(kFastWarps * EXW + N) * sizeof(float2);
 };
 
@@ -91,16 +93,16 @@ struct PencilFft {
 
 // grid.x = number of slabs (volumes * N); in and out may alias.
 template <int N, int S>
-__global__ void __launch_bounds__(kFastThreads, 1)
+__global__ void __launch_bounds__(kSlabThreads, 1)
 fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* slab = reinterpret_cast<float2*>(smem_raw);
     float2* exall = slab + N * LD;
-    float2* tw = exall + kFastWarps * L::EXW;
+    float2* tw = exall + kSlabWarps * L::EXW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < N; t += kSlabThreads) tw[t] = twg[t];
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * N * N;
 
@@ -108,7 +110,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     {
         const int p = lane / G, j = lane % G;
         float2* ex = exall + warp * L::EXW + p * L::EXP;
-        for (int r0 = 0; r0 < N; r0 += kFastWarps * PPW) {
+        for (int r0 = 0; r0 < N; r0 += kSlabWarps * PPW) {
             const int r = r0 + warp * PPW + p;
             const bool act = r < N;   // warp-uniform: N is a multiple of PPW
             if (act) {
@@ -132,7 +134,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     {
         const int cl = lane % PPW, j = lane / PPW;
         float2* ex = exall + warp * L::EXW + cl * L::EXP;
-        for (int c0 = 0; c0 < N; c0 += kFastWarps * PPW) {
+        for (int c0 = 0; c0 < N; c0 += kSlabWarps * PPW) {
             const int c = c0 + warp * PPW + cl;
             if (c0 + warp * PPW < N) {
                 float vr[R1], vi[R1];
@@ -151,6 +153,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     }
 }
 
+// Two pencils (adjacent columns c, c+1) per thread, 16-byte accesses.
 // grid.x = volumes * N (b) * ceil(N / CPB) column blocks; pencils along the
 // slowest axis.  in and out may alias.
 template <int N, int S>
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW;
-    constexpr int CPB = kFastWarps * PPW;
+    constexpr int CPB = kFastWarps * PPW * 2;
     constexpr int CBLK = (N + CPB - 1) / CPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* exall = reinterpret_cast<float2*>(smem_raw);
@@ -172,21 +175,62 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg)
     const int b = rem / CBLK;
     const int cb = rem % CBLK;
     const int cl = lane % PPW, j = lane / PPW;
-    const int c = cb * CPB + warp * PPW + cl;
-    if (cb * CPB + warp * PPW >= N) return;   // warp-uniform
+    const int c = cb * CPB + 2 * (warp * PPW + cl);
+    if (cb * CPB + 2 * warp * PPW >= N) return;   // warp-uniform (N is a multiple of 2 PPW)
     float2* ex = exall + warp * L::EXW + cl * L::EXP;
     const int64_t NN = (int64_t)N * N;
     const int64_t base = vol * NN * N + (int64_t)b * N + c;
-    float vr[R1], vi[R1];
+    float ar[R1], ai[R1], br[R1], bi[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
-        const float2 t = in[base + (int64_t)(j + G * m) * NN];
-        vr[m] = t.x;
-        vi[m] = t.y;
+        const float4 t = *reinterpret_cast<const float4*>(in + base + (int64_t)(j + G * m) * NN);
+        ar[m] = t.x;
+        ai[m] = t.y;
+        br[m] = t.z;
+        bi[m] = t.w;
     }
-    PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int a, float xr, float xi) {
-        out[base + (int64_t)a * NN] = make_float2(xr, xi);
-    });
+    // pencil c, then pencil c+1 through the same exchange slot; keep the
+    // length-G inputs of both, then emit 16-byte stores
+    constexpr int E = R1 / G;
+    float ur[2][E][G], ui[2][E][G];
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz) {
+        float* vr = pz ? br : ar;
+        float* vi = pz ? bi : ai;
+        reg::Dft<R1, S, float>::run(vr, vi);
+#pragma unroll
+        for (int k2 = 1; k2 < R1; ++k2) {
+            const float2 w = tw[(j * k2) % N];
+            const float wi = S > 0 ? w.y : -w.y;
+            const float t = vr[k2] * w.x - vi[k2] * wi;
+            vi[k2] = vr[k2] * wi + vi[k2] * w.x;
+            vr[k2] = t;
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < R1; ++k2) ex[j * (R1 + 1) + k2] = make_float2(vr[k2], vi[k2]);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj) {
+                const float2 t = ex[jj * (R1 + 1) + j + G * e];
+                ur[pz][e][jj] = t.x;
+                ui[pz][e][jj] = t.y;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        reg::Dft<G, S, float>::run(ur[0][e], ui[0][e]);
+        reg::Dft<G, S, float>::run(ur[1][e], ui[1][e]);
+        const int k2 = j + G * e;
+#pragma unroll
+        for (int k1 = 0; k1 < G; ++k1) {
+            *reinterpret_cast<float4*>(out + base + (int64_t)(k2 + R1 * k1) * NN) =
+                make_float4(ur[0][e][k1], ui[0][e][k1], ur[1][e][k1], ui[1][e][k1]);
+        }
+    }
 }
 
 }  // namespace fcc

@@ -1,36 +1,45 @@
 // Orbit mixing S, S^{-1}, S^H over tiles of representatives (FP32).
 //
-// One block per tile (<= kTileMax orbits) and volume, three phases:
-//   gather   for each slot g, warp lanes walk the tile along the direction
-//            that slot g maps to contiguous memory (c_dir[g]) and stage the
-//            24 slot values of every orbit in shared memory;
+// One warp per tile (<= 32 orbits forming a 4 x 4 x 2 box of
+// representatives); warps are independent (no block barrier).  Three phases:
+//   gather   for every slot g (unrolled, geometry known at compile time) each
+//            thread loads one value; lanes walk the tile along the direction
+//            slot g maps onto contiguous memory (wc::K::t.dir[g]).  All 24
+//            loads are in flight before the first shared-memory store;
 //   core     one thread per orbit: the class core (free orbits: c_core in
-//            constant memory, indices known at compile time) and the row
-//            phases R_g = exp(2 pi i (W_g kO).v / (8n));
-//   scatter  same walk as the gather, canonical slots only.
+//            constant memory) and the row phases R_g = w_{8n}^{(W_g kO).v};
+//   scatter  the same walk back to global memory, canonical slots only.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "plan.h"
+#include "weyl_const.h"
 
 namespace fcc {
 
 __constant__ float2 c_core[3][24][24];  // free-orbit cores: forward, inverse, adjoint
-__constant__ int c_dir[24];
+
+constexpr int kMaxClasses = 16;
 
 struct TiledMixArgs {
     const int32_t* tile_off;
     const uint32_t* reps;
     const uint8_t* cls;
-    const uint16_t* permb;
-    const uint16_t* permc;
+    const uint8_t* permb;
+    const uint8_t* permc;
     const float* mats;          // [ncls][24][24][2] core of this mode for every class
     const int8_t* wrap;         // [ncls][24][3]
     const uint32_t* canon_mask; // [ncls]
     const float2* phase;        // [8n]
+    // flat index of slot g of a free orbit: k . lin[g] + lin[g][3]; lin[g][0..2]
+    // are the columns of W_g weighted by (n^2, n, 1), lin[g][3] the wrap offset
+    int lin[24][4];
     int n;
+    int ncls;
     int free_class;
     int64_t n3;
     float scale;
@@ -38,73 +47,144 @@ struct TiledMixArgs {
 
 constexpr int kMixRow = 50;  // floats per orbit row in shared memory (24 complex + pad)
 
-__device__ __forceinline__ int tile_pick(int dir, int t, const uint16_t* pb, const uint16_t* pc) {
-    return dir == 1 ? (int)pb[t] : dir == 2 ? (int)pc[t] : t;
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
 }
 
-__device__ __forceinline__ int slot_index(int g, uint32_t rp, const int8_t* wr, int n) {
+// Compile-time entries of W (read only in constant expressions).
+template <int G, int I> struct WM { static constexpr int v = wc::K::t.m[G][I]; };
+template <int G, int I> struct WU { static constexpr int v = wc::K::t.u[G][I]; };
+template <int G, int I> struct WF { static constexpr int v = wc::K::t.fw[G][I]; };
+template <int G> struct WD { static constexpr int v = wc::K::t.dir[G]; };
+
+template <int G>
+__device__ __forceinline__ void slot_point(uint32_t rp, int& p0, int& p1, int& p2) {
     const int k0 = rp & 1023, k1 = (rp >> 10) & 1023, k2 = (rp >> 20) & 1023;
-    const int p0 = c_W[g][0] * k0 + c_W[g][1] * k1 + c_W[g][2] * k2 - n * wr[3 * g + 0];
-    const int p1 = c_W[g][3] * k0 + c_W[g][4] * k1 + c_W[g][5] * k2 - n * wr[3 * g + 1];
-    const int p2 = c_W[g][6] * k0 + c_W[g][7] * k1 + c_W[g][8] * k2 - n * wr[3 * g + 2];
+    p0 = WM<G, 0>::v * k0 + WM<G, 1>::v * k1 + WM<G, 2>::v * k2;
+    p1 = WM<G, 3>::v * k0 + WM<G, 4>::v * k1 + WM<G, 5>::v * k2;
+    p2 = WM<G, 6>::v * k0 + WM<G, 7>::v * k1 + WM<G, 8>::v * k2;
+}
+
+// flat index of slot G of representative rp for a free orbit (compile-time wrap)
+template <int G>
+__device__ __forceinline__ int slot_idx_free(uint32_t rp, int n) {
+    int p0, p1, p2;
+    slot_point<G>(rp, p0, p1, p2);
+    p0 -= n * WF<G, 0>::v;
+    p1 -= n * WF<G, 1>::v;
+    p2 -= n * WF<G, 2>::v;
     return (p0 * n + p1) * n + p2;
 }
 
-__device__ __forceinline__ int phase_exp(int g, uint32_t rp, int M8) {
+template <int G>
+__device__ __forceinline__ int slot_idx_gen(uint32_t rp, const int8_t* wr, int n) {
+    int p0, p1, p2;
+    slot_point<G>(rp, p0, p1, p2);
+    p0 -= n * wr[3 * G + 0];
+    p1 -= n * wr[3 * G + 1];
+    p2 -= n * wr[3 * G + 2];
+    return (p0 * n + p1) * n + p2;
+}
+
+template <int G>
+__device__ __forceinline__ int slot_phase(uint32_t rp, int M8) {
     const int k0 = rp & 1023, k1 = (rp >> 10) & 1023, k2 = (rp >> 20) & 1023;
-    int e = (c_u[g][0] * k0 + c_u[g][1] * k1 + c_u[g][2] * k2) % M8;
+    int e = (WU<G, 0>::v * k0 + WU<G, 1>::v * k1 + WU<G, 2>::v * k2) % M8;
     return e < 0 ? e + M8 : e;
 }
 
-template <int MODE, bool RIN, bool ROUT>
-__global__ void __launch_bounds__(kTileMax) mix_tiled_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                             TiledMixArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* rows = reinterpret_cast<float*>(smem_raw);                 // [kTileMax][kMixRow]
-    float2* ph = reinterpret_cast<float2*>(rows + kTileMax * kMixRow);  // [8n]
-    uint32_t* s_rep = reinterpret_cast<uint32_t*>(ph + 8 * a.n);
-    uint16_t* s_pb = reinterpret_cast<uint16_t*>(s_rep + kTileMax);
-    uint16_t* s_pc = s_pb + kTileMax;
-    uint8_t* s_cls = reinterpret_cast<uint8_t*>(s_pc + kTileMax);
+constexpr int kMixWarps = 8;                 // warps (= independent tiles) per block
+constexpr int kMixThreads = 32 * kMixWarps;
 
-    const int tile = blockIdx.x;
-    const int64_t vol = blockIdx.y;
+__device__ __forceinline__ int rep_dot(uint32_t rp, int a0, int a1, int a2) {
+    return (int)(rp & 1023) * a0 + (int)((rp >> 10) & 1023) * a1 + (int)((rp >> 20) & 1023) * a2;
+}
+
+// flat index of slot G: affine in the representative; non-free orbits take
+// their class's wrap vector instead of the free one
+template <int G>
+__device__ __forceinline__ int slot_flat(const TiledMixArgs& a, uint32_t rp, bool free_orbit, int cls) {
+    const int lin = rep_dot(rp, a.lin[G][0], a.lin[G][1], a.lin[G][2]);
+    if (free_orbit) return lin + a.lin[G][3];
+    const int8_t* wr = a.wrap + 72 * cls + 3 * G;
+    const int n = a.n;
+    return lin - n * ((int)__ldg(wr) * n * n + (int)__ldg(wr + 1) * n + (int)__ldg(wr + 2));
+}
+
+// row-phase exponent (W_G kO).v mod 8n, v = (1, 0, 3)
+template <int G>
+__device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
+    const int q = rep_dot(rp, WU<G, 0>::v, WU<G, 1>::v, WU<G, 2>::v);
+    return q < 0 ? q + M8 : q;
+}
+
+// grid.x covers the tiles (kMixWarps per block), grid.y the volumes.
+template <int MODE, bool RIN, bool ROUT>
+__global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
+                                                                   float* __restrict__ out, const TiledMixArgs a,
+                                                                   int ntiles) {
+    constexpr bool CIN = (MODE != MODE_FWD) || !RIN;   // complex input values
+    constexpr bool COUT = (MODE == MODE_FWD) || !ROUT; // complex output values
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
+    const int tile = blockIdx.x * kMixWarps + warp;
+    if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
+    const int64_t base = (int64_t)blockIdx.y * a.n3;
     const int o0 = a.tile_off[tile];
     const int cnt = a.tile_off[tile + 1] - o0;
-    const int t = threadIdx.x;
-    const int n = a.n, M8 = 8 * n;
-    if (t < cnt) {
-        s_rep[t] = a.reps[o0 + t];
-        s_cls[t] = a.cls[o0 + t];
-        s_pb[t] = a.permb[o0 + t];
-        s_pc[t] = a.permc[o0 + t];
+    const int M8 = 8 * a.n;
+    const bool act = lane < cnt;
+    uint32_t myrep = 0;
+    int mycls = a.free_class < 0 ? 0 : a.free_class;
+    int rsel[4] = {lane, lane, lane, lane};
+    if (act) {
+        myrep = __ldg(a.reps + o0 + lane);
+        mycls = __ldg(a.cls + o0 + lane);
+        rsel[1] = __ldg(a.permb + o0 + lane);
+        rsel[2] = __ldg(a.permc + o0 + lane);
     }
-    for (int e = t; e < M8; e += blockDim.x) ph[e] = a.phase[e];
-    __syncthreads();
+    const bool free_orbit = mycls == a.free_class;
+    const uint32_t mycanon = free_orbit ? 0xffffffu : __ldg(a.canon_mask + mycls);
+    const float2* __restrict__ ph = a.phase;
 
-    // gather: forward reads x (real or complex); inverse/adjoint read Z (complex)
-    constexpr bool CIN = (MODE != MODE_FWD) || !RIN;
-    const int64_t in_base = vol * a.n3;
-    if (t < cnt) {
-        for (int g = 0; g < 24; ++g) {
-            const int r = tile_pick(c_dir[g], t, s_pb, s_pc);
-            const uint32_t rp = s_rep[r];
-            const int idx = slot_index(g, rp, a.wrap + 72 * s_cls[r], n);
-            if (CIN) {
-                const float2 v = reinterpret_cast<const float2*>(in)[in_base + idx];
-                *reinterpret_cast<float2*>(rows + r * kMixRow + 2 * g) = v;
-            } else {
-                rows[r * kMixRow + 2 * g] = in[in_base + idx];
+    // ---- gather: lanes walk the tile in the order slot g maps to memory;
+    // the owning lane computes each index and shuffles it over
+    {
+        float vr[24], vi[24];
+        static_for<0, 24>([&](auto Gc) {
+            constexpr int g = decltype(Gc)::value;
+            const int r = rsel[WD<g>::v];
+            const int gi = __shfl_sync(0xffffffffu, slot_flat<g>(a, myrep, free_orbit, mycls), r);
+            vr[g] = 0.f;
+            vi[g] = 0.f;
+            if (act) {
+                if (CIN) {
+                    const float2 v = __ldg(reinterpret_cast<const float2*>(in) + base + gi);
+                    vr[g] = v.x;
+                    vi[g] = v.y;
+                } else {
+                    vr[g] = __ldg(in + base + gi);
+                }
             }
+        });
+        if (act) {
+            static_for<0, 24>([&](auto Gc) {
+                constexpr int g = decltype(Gc)::value;
+                const int r = rsel[WD<g>::v];
+                if (CIN) *reinterpret_cast<float2*>(rows + r * kMixRow + 2 * g) = make_float2(vr[g], vi[g]);
+                else rows[r * kMixRow + 2 * g] = vr[g];
+            });
         }
     }
-    __syncthreads();
-
-    // core: one thread per orbit, in place in its own row
-    if (t < cnt) {
-        float* row = rows + t * kMixRow;
-        const uint32_t rp = s_rep[t];
-        const int c = s_cls[t];
+    __syncwarp();
+    // ---- core: lane = orbit, in place in its own row
+    if (act) {
+        float* row = rows + lane * kMixRow;
         float xr[24], xi[24];
 #pragma unroll
         for (int h = 0; h < 24; ++h) {
@@ -118,21 +198,18 @@ __global__ void __launch_bounds__(kTileMax) mix_tiled_kernel(const float* __rest
             }
         }
         if (MODE != MODE_FWD) {
-            // t_g = conj(R_g) Z_g
-#pragma unroll
-            for (int g = 0; g < 24; ++g) {
-                const float2 R = ph[phase_exp(g, rp, M8)];
+            static_for<0, 24>([&](auto Gc) {
+                constexpr int g = decltype(Gc)::value;
+                const float2 R = __ldg(ph + slot_exp<g>(myrep, M8));
                 const float zr = xr[g], zi = xi[g];
-                xr[g] = R.x * zr + R.y * zi;
+                xr[g] = R.x * zr + R.y * zi;  // conj(R) Z
                 xi[g] = R.x * zi - R.y * zr;
-            }
+            });
         }
-        const bool fast = c == a.free_class;
-        const float* M = a.mats + (size_t)c * 1152;
-#pragma unroll
-        for (int g = 0; g < 24; ++g) {
-            float ar = 0.f, ai = 0.f;
-            if (fast) {
+        if (free_orbit) {
+            static_for<0, 24>([&](auto Gc) {
+                constexpr int g = decltype(Gc)::value;
+                float ar = 0.f, ai = 0.f;
 #pragma unroll
                 for (int h = 0; h < 24; ++h) {
                     const float2 m = c_core[MODE][g][h];
@@ -143,7 +220,23 @@ __global__ void __launch_bounds__(kTileMax) mix_tiled_kernel(const float* __rest
                         ai = fmaf(m.x, xi[h], ai);
                     }
                 }
-            } else {
+                if (MODE == MODE_FWD) {
+                    const float2 R = __ldg(ph + slot_exp<g>(myrep, M8));
+                    *reinterpret_cast<float2*>(row + 2 * g) =
+                        make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
+                } else if (ROUT) {
+                    row[2 * g] = a.scale * ar;
+                } else {
+                    *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * ar, a.scale * ai);
+                }
+            });
+        } else {
+            // rare (orbits on the alcove boundary): class core from global memory
+            const float* M = a.mats + (size_t)mycls * 1152;
+#pragma unroll 1
+            for (int g = 0; g < 24; ++g) {
+                float ar = 0.f, ai = 0.f;
+#pragma unroll
                 for (int h = 0; h < 24; ++h) {
                     const float mr = __ldg(M + 2 * (g * 24 + h)), mi = __ldg(M + 2 * (g * 24 + h) + 1);
                     ar = fmaf(mr, xr[h], ar);
@@ -153,39 +246,38 @@ __global__ void __launch_bounds__(kTileMax) mix_tiled_kernel(const float* __rest
                         ai = fmaf(mr, xi[h], ai);
                     }
                 }
-            }
-            if (MODE == MODE_FWD) {
-                const float2 R = ph[phase_exp(g, rp, M8)];
-                const float zr = R.x * ar - R.y * ai, zi = R.x * ai + R.y * ar;
-                *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * zr, a.scale * zi);
-            } else if (ROUT) {
-                row[2 * g] = a.scale * ar;
-            } else {
-                *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * ar, a.scale * ai);
-            }
-        }
-    }
-    __syncthreads();
-
-    // scatter canonical slots
-    const bool COUT = (MODE == MODE_FWD) || !ROUT;
-    if (t < cnt) {
-        for (int g = 0; g < 24; ++g) {
-            const int r = tile_pick(c_dir[g], t, s_pb, s_pc);
-            const int c = s_cls[r];
-            if (!((a.canon_mask[c] >> g) & 1u)) continue;
-            const int idx = slot_index(g, s_rep[r], a.wrap + 72 * c, n);
-            if (COUT) {
-                reinterpret_cast<float2*>(out)[in_base + idx] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
-            } else {
-                out[in_base + idx] = rows[r * kMixRow + 2 * g];
+                if (MODE == MODE_FWD) {
+                    int q = (int)(myrep & 1023) * c_u[g][0] + (int)((myrep >> 10) & 1023) * c_u[g][1] +
+                            (int)((myrep >> 20) & 1023) * c_u[g][2];
+                    q = q < 0 ? q + M8 : q;
+                    const float2 R = __ldg(ph + q);
+                    *reinterpret_cast<float2*>(row + 2 * g) =
+                        make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
+                } else if (ROUT) {
+                    row[2 * g] = a.scale * ar;
+                } else {
+                    *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * ar, a.scale * ai);
+                }
             }
         }
     }
+    __syncwarp();
+    // ---- scatter canonical slots
+    const uint32_t can_d[3] = {mycanon, __shfl_sync(0xffffffffu, mycanon, rsel[1]),
+                               __shfl_sync(0xffffffffu, mycanon, rsel[2])};
+    static_for<0, 24>([&](auto Gc) {
+        constexpr int g = decltype(Gc)::value;
+        constexpr int d = WD<g>::v;
+        const int r = rsel[d];
+        const int gi = __shfl_sync(0xffffffffu, slot_flat<g>(a, myrep, free_orbit, mycls), r);
+        const uint32_t cm = d == 1 ? can_d[1] : d == 2 ? can_d[2] : can_d[0];
+        if (act && ((cm >> g) & 1u)) {
+            if (COUT) reinterpret_cast<float2*>(out)[base + gi] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
+            else out[base + gi] = rows[r * kMixRow + 2 * g];
+        }
+    });
 }
 
-inline size_t mix_tiled_smem(int n) {
-    return (size_t)kTileMax * kMixRow * 4 + (size_t)8 * n * 8 + kTileMax * (4 + 2 + 2 + 1) + 16;
-}
+inline size_t mix_tiled_smem(int) { return (size_t)kMixWarps * 32 * kMixRow * 4; }
 
 }  // namespace fcc

@@ -270,16 +270,18 @@ int build_host_plan(int n, HostPlan& P) {
     // Tiles.
     struct Item { int64_t key; int a, b, c; uint32_t rep; uint8_t cls; };
     std::vector<Item> items(P.reps.size());
-    const int nta = n / kTileA + 1, ntb = n / kTileB + 1, ntc = n / kTileC + 1;
     for (size_t o = 0; o < P.reps.size(); ++o) {
         const int k1 = P.reps[o] & 1023, k2 = (P.reps[o] >> 10) & 1023, k3 = (P.reps[o] >> 20) & 1023;
         const int a = k1 + k2 + k3, b = k1 + k2, c = k1;
-        const int64_t tk = ((int64_t)(a / kTileA) * ntb + b / kTileB) * ntc + c / kTileC;
+        // super-box first so that consecutive tiles (one block) are neighbours
+        const int64_t sk = ((int64_t)(a / kSuperA) * (n / kSuperB + 1) + b / kSuperB) * (n / kSuperC + 1) + c / kSuperC;
+        const int sub = (((a % kSuperA) / kTileA) * (kSuperB / kTileB) + (b % kSuperB) / kTileB) * (kSuperC / kTileC) +
+                        (c % kSuperC) / kTileC;
+        const int64_t tk = sk * 64 + sub;
         // a' fastest inside the tile
         const int64_t local = ((int64_t)(c % kTileC) * kTileB + b % kTileB) * kTileA + a % kTileA;
         items[o] = {tk * kTileMax + local, a, b, c, P.reps[o], P.cls[o]};
     }
-    (void)nta;
     std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.key < y.key; });
     P.tile_off.clear();
     P.tile_reps.resize(items.size());
@@ -306,7 +308,7 @@ int build_host_plan(int n, HostPlan& P) {
             if (X.c != Y.c) return X.c < Y.c;
             return X.b < Y.b;
         });
-        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_b[i + t] = (uint16_t)ord[t];
+        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_b[i + t] = (uint8_t)ord[t];
         std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
             const Item& X = items[i + x];
             const Item& Y = items[i + y];
@@ -314,7 +316,7 @@ int build_host_plan(int n, HostPlan& P) {
             if (X.b != Y.b) return X.b < Y.b;
             return X.c < Y.c;
         });
-        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_c[i + t] = (uint16_t)ord[t];
+        for (size_t t = 0; t < ord.size(); ++t) P.tile_perm_c[i + t] = (uint8_t)ord[t];
         i = e;
     }
     P.tile_off.push_back((int32_t)items.size());

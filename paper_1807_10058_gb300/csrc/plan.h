@@ -77,13 +77,14 @@ struct HostPlan {
     std::vector<int32_t> tile_off;   // [ntiles + 1], offsets into tile_reps
     std::vector<uint32_t> tile_reps; // packed representatives, tile order
     std::vector<uint8_t> tile_cls;
-    std::vector<uint16_t> tile_perm_b;
-    std::vector<uint16_t> tile_perm_c;
+    std::vector<uint8_t> tile_perm_b;
+    std::vector<uint8_t> tile_perm_c;
     int max_tile = 0;
 };
 
-constexpr int kTileA = 8, kTileB = 8, kTileC = 4;
+constexpr int kTileA = 4, kTileB = 4, kTileC = 2;   // one warp per tile
 constexpr int kTileMax = kTileA * kTileB * kTileC;
+constexpr int kSuperA = 8, kSuperB = 8, kSuperC = 4;  // tiles of one block are adjacent
 
 // For slot g, the direction in (a', b', c') along which consecutive
 // representatives map to consecutive memory: 0 = a', 1 = b', 2 = c',
