@@ -77,6 +77,7 @@ struct fcc_plan {
     // with the caller's stream through events)
     int64_t chunk_bytes = 32ll << 20;
     int nstreams = 2;
+    bool pairing = true;             // real dtypes: two volumes per complex transform
     cudaStream_t streams[kMaxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kMaxStreams] = {};
@@ -252,6 +253,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
     if (s == FCC_OK) {
         if (const char* e = std::getenv("FCC_CHUNK_MB")) p->chunk_bytes = std::max(1, std::atoi(e)) * (1ll << 20);
         if (const char* e = std::getenv("FCC_STREAMS")) p->nstreams = std::min(kMaxStreams, std::max(1, std::atoi(e)));
+        if (const char* e = std::getenv("FCC_PAIRING")) p->pairing = std::atoi(e) != 0;
         for (int i = 0; i < p->nstreams && s == FCC_OK; ++i) {
             if (cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
@@ -384,7 +386,7 @@ fcc_status launch_mix(const OrderTables& t, int mode, bool real_in, bool real_ou
 
 template <int N>
 fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out, int64_t nvol, const float2* tw,
-                             cudaStream_t st) {
+                             int64_t vstride, cudaStream_t st) {
     using L = FastLayout<N>;
     if (slab) {
         static bool attr = false;
@@ -395,8 +397,8 @@ fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out,
         }
         ProfScope ps("fft_slab", st);
         const unsigned grid = (unsigned)(nvol * N);
-        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw);
-        else fft_slab_kernel<N, -1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw);
+        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw, vstride);
+        else fft_slab_kernel<N, -1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw, vstride);
     } else {
         static bool attr = false;
         if (!attr) {
@@ -407,8 +409,8 @@ fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out,
         constexpr int CPB = kFastWarps * L::PPW * 2;
         const unsigned grid = (unsigned)(nvol * N * ((N + CPB - 1) / CPB));
         ProfScope ps("fft_pencil", st);
-        if (sign > 0) fft_pencil_kernel<N, 1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw);
-        else fft_pencil_kernel<N, -1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw);
+        if (sign > 0) fft_pencil_kernel<N, 1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
+        else fft_pencil_kernel<N, -1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
     }
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
@@ -421,19 +423,19 @@ bool has_fast_fft(int n) {
 }
 
 fcc_status launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
-                           const float2* tw, cudaStream_t st) {
+                           const float2* tw, int64_t vstride, cudaStream_t st) {
     switch (n) {
-        case 128: return launch_fast_fft_n<128>(slab, sign, in, out, nvol, tw, st);
-        case 96: return launch_fast_fft_n<96>(slab, sign, in, out, nvol, tw, st);
-        case 64: return launch_fast_fft_n<64>(slab, sign, in, out, nvol, tw, st);
-        case 32: return launch_fast_fft_n<32>(slab, sign, in, out, nvol, tw, st);
-        case 16: return launch_fast_fft_n<16>(slab, sign, in, out, nvol, tw, st);
+        case 128: return launch_fast_fft_n<128>(slab, sign, in, out, nvol, tw, vstride, st);
+        case 96: return launch_fast_fft_n<96>(slab, sign, in, out, nvol, tw, vstride, st);
+        case 64: return launch_fast_fft_n<64>(slab, sign, in, out, nvol, tw, vstride, st);
+        case 32: return launch_fast_fft_n<32>(slab, sign, in, out, nvol, tw, vstride, st);
+        case 16: return launch_fast_fft_n<16>(slab, sign, in, out, nvol, tw, vstride, st);
         default: return FCC_ERR_UNSUPPORTED;
     }
 }
 
 fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
-                            float* out, int64_t nvol, float scale, cudaStream_t st) {
+                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false) {
     TiledMixArgs a;
     a.tile_off = t.tile_off;
     a.reps = t.tile_reps;
@@ -468,15 +470,29 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
         cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         attr = true;
     }
     static const char* names[3] = {"mix_tiled_fwd", "mix_tiled_inv", "mix_tiled_adj"};
     for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
         const int64_t nv = std::min<int64_t>(65535, nvol - v0);
         dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
+        const int nt = t.ntiles;
+        if (pair) {
+            // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes;
+            // inverse / adjoint: compact complex -> real volumes 2p, 2p+1
+            const float* src = in + v0 * a.n3 * 2;
+            float* dst = out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
+            ProfScope ps(names[mode], st);
+            if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            continue;
+        }
         const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
         float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
-        const int nt = t.ntiles;
         ProfScope ps(names[mode], st);
         if (mode == MODE_FWD) {
             if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
@@ -494,21 +510,51 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
 
 // 3-D DFT of nvol complex volumes: fast slab + pencil passes when the order
 // has a register factorisation, else the generic pass per axis.
-fcc_status launch_dft3(const OrderTables& t, int sign, const float* in, float* out, int64_t nvol, cudaStream_t st) {
+// volume v of in and out starts at v * vstride complex values.
+fcc_status launch_dft3(const OrderTables& t, int sign, const float* in, float* out, int64_t nvol, cudaStream_t st,
+                       int64_t vstride = 0) {
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    if (vstride == 0) vstride = n3;
     if (has_fast_fft(t.n)) {
         const float2* tw = (const float2*)t.tw;
         fcc_status s;
         if (sign > 0) {
-            if ((s = launch_fast_fft(t.n, true, sign, (const float2*)in, (float2*)out, nvol, tw, st))) return s;
-            return launch_fast_fft(t.n, false, sign, (const float2*)out, (float2*)out, nvol, tw, st);
+            if ((s = launch_fast_fft(t.n, true, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
+            return launch_fast_fft(t.n, false, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
         }
-        if ((s = launch_fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, st))) return s;
-        return launch_fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, st);
+        if ((s = launch_fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
+        return launch_fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
     }
-    fcc_status s = launch_fft<float>(t, in, out, nvol, 0, sign, st);
-    if (!s) s = launch_fft<float>(t, out, out, nvol, 1, sign, st);
-    if (!s) s = launch_fft<float>(t, out, out, nvol, 2, sign, st);
+    // generic passes work on contiguous volumes: one launch set per volume when strided
+    fcc_status s = FCC_OK;
+    const int64_t step = vstride == n3 ? nvol : 1;
+    for (int64_t v = 0; v < nvol && !s; v += step) {
+        const int64_t nv = std::min(step, nvol - v);
+        const float* src = in + 2 * v * vstride;
+        float* dst = out + 2 * v * vstride;
+        s = launch_fft<float>(t, src, dst, nv, 0, sign, st);
+        if (!s) s = launch_fft<float>(t, dst, dst, nv, 1, sign, st);
+        if (!s) s = launch_fft<float>(t, dst, dst, nv, 2, sign, st);
+    }
     return s;
+}
+
+fcc_status launch_pair(bool split, int n, const float* in, float* out, int64_t npairs, cudaStream_t st) {
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t per_pair = (int64_t)n * n * (n / 2 + 1);
+    for (int64_t p0 = 0; p0 < npairs; p0 += 65535) {
+        const int64_t np = std::min<int64_t>(65535, npairs - p0);
+        dim3 grid((unsigned)((per_pair + 255) / 256), (unsigned)np);
+        if (split) {
+            ProfScope ps("pair_split", st);
+            pair_split_kernel<<<grid, 256, 0, st>>>((float2*)out + p0 * 2 * n3, n, n3, per_pair);
+        } else {
+            ProfScope ps("pair_merge", st);
+            pair_merge_kernel<<<grid, 256, 0, st>>>((const float2*)in + p0 * 2 * n3, (float2*)out + p0 * n3, n, n3,
+                                                    per_pair);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
 int64_t chunk_vols(const fcc_plan* p, int n) {
@@ -529,7 +575,30 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
         if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
     fcc_status s = FCC_OK;
     int c = 0;
-    for (int64_t v0 = 0; v0 < nvol && !s; v0 += cv, ++c) {
+    // real dtypes: two real volumes per complex transform (see pair_split_kernel)
+    const bool pairing = rin && p->pairing && nvol >= 2;
+    const int64_t npairs = pairing ? nvol / 2 : 0;
+    const int64_t cp = cv;   // pairs per chunk: one complex volume of intermediate per pair
+    for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
+        const int64_t np = std::min(cp, npairs - p0);
+        cudaStream_t ss = p->streams[c % ns];
+        if (which == 0) {
+            const float* x = in + 2 * p0 * n3;
+            float* y = out + 2 * p0 * n3 * 2;
+            s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true);
+            if (!s) s = launch_dft3(t, +1, y, y, np, ss, 2 * n3);
+            if (!s) s = launch_pair(true, t.n, nullptr, y, np, ss);
+        } else {
+            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            const float* y = in + 2 * p0 * n3 * 2;
+            float* x = out + 2 * p0 * n3;
+            s = launch_pair(false, t.n, y, ws, np, ss);
+            if (!s) s = launch_dft3(t, -1, ws, ws, np, ss);
+            const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
+            if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, true, ws, x, np, scale, ss, true);
+        }
+    }
+    for (int64_t v0 = 2 * npairs; v0 < nvol && !s; v0 += cv, ++c) {
         const int64_t nv = std::min(cv, nvol - v0);
         cudaStream_t ss = p->streams[c % ns];
         if (which == 0) {
@@ -686,8 +755,14 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         const int mix = (int)((nv + 65534) / 65535);
         if (!is_double(p->dtype) && n > 1) {
             const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
-            const int64_t chunks = (nv + cv - 1) / cv;
-            total += (int)(chunks * (1 + (has_fast_fft(n) ? 2 : 3)));
+            const int dft = has_fast_fft(n) ? 2 : 3;
+            const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
+            const int64_t npairs = pairing ? nv / 2 : 0;
+            const int64_t pchunks = (npairs + cv - 1) / cv;
+            const int64_t dft_per_pchunk = has_fast_fft(n) ? 2 : 3 * cv;   // generic passes go volume by volume
+            total += (int)(pchunks * (2 + dft_per_pchunk));
+            const int64_t rest = nv - 2 * npairs;
+            total += (int)(((rest + cv - 1) / cv) * (1 + dft));
         } else if (which == 0) total += mix + 3;
         else {
             const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);

@@ -91,10 +91,11 @@ struct PencilFft {
     }
 };
 
-// grid.x = number of slabs (volumes * N); in and out may alias.
+// grid.x = number of slabs (volumes * N); volume v starts at v * vstride
+// complex values; in and out may alias.
 template <int N, int S>
 __global__ void __launch_bounds__(kSlabThreads, 1)
-fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
+fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,7 +105,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < N; t += kSlabThreads) tw[t] = twg[t];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * N * N;
+    const int64_t base = (int64_t)(blockIdx.x / N) * vstride + (int64_t)(blockIdx.x % N) * N * N;
 
     // rows (fastest axis)
     {
@@ -158,7 +159,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
 // slowest axis.  in and out may alias.
 template <int N, int S>
 __global__ void __launch_bounds__(kFastThreads)
-fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg) {
+fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW;
     constexpr int CPB = kFastWarps * PPW * 2;
@@ -179,7 +180,7 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg)
     if (cb * CPB + 2 * warp * PPW >= N) return;   // warp-uniform (N is a multiple of 2 PPW)
     float2* ex = exall + warp * L::EXW + cl * L::EXP;
     const int64_t NN = (int64_t)N * N;
-    const int64_t base = vol * NN * N + (int64_t)b * N + c;
+    const int64_t base = vol * vstride + (int64_t)b * N + c;
     float ar[R1], ai[R1], br[R1], bi[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
@@ -231,6 +232,71 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg)
                 make_float4(ur[0][e][k1], ui[0][e][k1], ur[1][e][k1], ui[1][e][k1]);
         }
     }
+}
+
+}  // namespace fcc
+
+namespace fcc {
+
+// --- pairing of two real volumes ------------------------------------------
+//
+// For real x the rows of DCT_n come in conjugate pairs: (D x)[pi(i,l,q)] =
+// conj((D x)[i,l,q]) with pi(i,l,q) = (i-l, -l, q-l) mod n, an involution.
+// Hence one complex transform Y = D (x1 + i x2) gives
+//   D x1 = (Y + conj(Y o pi)) / 2,   D x2 = (Y - conj(Y o pi)) / (2i),
+// and with P(v) = (v + conj(v o pi)) / 2 one has Re(D^-1 v) = D^-1 P(v) and
+// Re(D^H v) = D^H P(v), so P(v1) + i P(v2) pairs the inverse and adjoint.
+
+// Threads enumerate (i, l, q) with 0 <= l <= n/2; each handles one point a
+// and its partner b = pi(a) (a alone when l = 0, only i < n/2 when 2l = n).
+__device__ __forceinline__ bool pair_point(int64_t t, int n, int& a, int& b) {
+    const int q = (int)(t % n);
+    const int i = (int)((t / n) % n);
+    const int l = (int)(t / ((int64_t)n * n));
+    if (2 * l == n && i >= n / 2) return false;
+    a = (i * n + l) * n + q;
+    const int i2 = (i - l + n) % n, l2 = (n - l) % n, q2 = (q - l + n) % n;
+    b = (i2 * n + l2) * n + q2;
+    return true;
+}
+
+// Y (complex) at volume 2p of y -> D x1 into volume 2p, D x2 into 2p+1.
+__global__ void pair_split_kernel(float2* y, int n, int64_t n3, int64_t per_pair) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= per_pair) return;
+    int a, b;
+    if (!pair_point(t, n, a, b)) return;
+    float2* Y = y + (int64_t)blockIdx.y * 2 * n3;
+    float2* Y2 = Y + n3;
+    const float2 ya = Y[a], yb = Y[b];
+    // y1[a] = (ya + conj(yb))/2, y2[a] = (ya - conj(yb))/(2i) = -i (ya - conj(yb))/2
+    const float2 s1a = make_float2(0.5f * (ya.x + yb.x), 0.5f * (ya.y - yb.y));
+    const float2 d1a = make_float2(0.5f * (ya.x - yb.x), 0.5f * (ya.y + yb.y));
+    const float2 s1b = make_float2(s1a.x, -s1a.y);                    // (yb + conj(ya))/2 = conj(s1a)
+    const float2 d1b = make_float2(-d1a.x, d1a.y);                    // (yb - conj(ya))/2 = -conj(d1a)
+    Y[a] = s1a;
+    Y[b] = s1b;
+    Y2[a] = make_float2(d1a.y, -d1a.x);
+    Y2[b] = make_float2(d1b.y, -d1b.x);
+}
+
+// v1, v2 (complex, volumes 2p and 2p+1 of y) -> W = P(v1) + i P(v2) at
+// volume p of w.
+__global__ void pair_merge_kernel(const float2* __restrict__ y, float2* __restrict__ w, int n, int64_t n3,
+                                  int64_t per_pair) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= per_pair) return;
+    int a, b;
+    if (!pair_point(t, n, a, b)) return;
+    const float2* V1 = y + (int64_t)blockIdx.y * 2 * n3;
+    const float2* V2 = V1 + n3;
+    float2* W = w + (int64_t)blockIdx.y * n3;
+    const float2 pa = V1[a], pb = V1[b], qa = V2[a], qb = V2[b];
+    const float2 P1 = make_float2(0.5f * (pa.x + pb.x), 0.5f * (pa.y - pb.y));   // P(v1)[a]
+    const float2 P2 = make_float2(0.5f * (qa.x + qb.x), 0.5f * (qa.y - qb.y));   // P(v2)[a]
+    // W[a] = P1 + i P2 ; W[b] = conj(P1) + i conj(P2)
+    W[a] = make_float2(P1.x - P2.y, P1.y + P2.x);
+    W[b] = make_float2(P1.x + P2.y, -P1.y + P2.x);
 }
 
 }  // namespace fcc

@@ -122,19 +122,23 @@ __device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
     return q < 0 ? q + M8 : q;
 }
 
-// grid.x covers the tiles (kMixWarps per block), grid.y the volumes.
-template <int MODE, bool RIN, bool ROUT>
+// grid.x covers the tiles (kMixWarps per block), grid.y the volumes (pairs
+// of real volumes when PAIR: forward reads x1 + i x2 from volumes 2p, 2p+1
+// and writes Z to volume 2p of the complex output; inverse / adjoint read a
+// compact complex volume p and write Re / Im to real volumes 2p, 2p+1).
+template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
 __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
                                                                    float* __restrict__ out, const TiledMixArgs a,
                                                                    int ntiles) {
-    constexpr bool CIN = (MODE != MODE_FWD) || !RIN;   // complex input values
-    constexpr bool COUT = (MODE == MODE_FWD) || !ROUT; // complex output values
+    constexpr bool CIN = (MODE != MODE_FWD) || !RIN || PAIR;    // complex values in the core
+    constexpr bool COUT = (MODE == MODE_FWD) || !ROUT || PAIR;  // complex values out of the core
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
     const int tile = blockIdx.x * kMixWarps + warp;
     if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
-    const int64_t base = (int64_t)blockIdx.y * a.n3;
+    const int64_t base = (int64_t)blockIdx.y * a.n3;   // unpaired volume offset (values)
+    const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;  // paired: first volume of the pair
     const int o0 = a.tile_off[tile];
     const int cnt = a.tile_off[tile + 1] - o0;
     const int M8 = 8 * a.n;
@@ -163,7 +167,10 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
             vr[g] = 0.f;
             vi[g] = 0.f;
             if (act) {
-                if (CIN) {
+                if (PAIR && MODE == MODE_FWD) {
+                    vr[g] = __ldg(in + pb + gi);
+                    vi[g] = __ldg(in + pb + a.n3 + gi);
+                } else if (CIN) {
                     const float2 v = __ldg(reinterpret_cast<const float2*>(in) + base + gi);
                     vr[g] = v.x;
                     vi[g] = v.y;
@@ -224,7 +231,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
                     const float2 R = __ldg(ph + slot_exp<g>(myrep, M8));
                     *reinterpret_cast<float2*>(row + 2 * g) =
                         make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
-                } else if (ROUT) {
+                } else if (ROUT && !PAIR) {
                     row[2 * g] = a.scale * ar;
                 } else {
                     *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * ar, a.scale * ai);
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
                     const float2 R = __ldg(ph + q);
                     *reinterpret_cast<float2*>(row + 2 * g) =
                         make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
-                } else if (ROUT) {
+                } else if (ROUT && !PAIR) {
                     row[2 * g] = a.scale * ar;
                 } else {
                     *reinterpret_cast<float2*>(row + 2 * g) = make_float2(a.scale * ar, a.scale * ai);
@@ -272,8 +279,17 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
         const int gi = __shfl_sync(0xffffffffu, slot_flat<g>(a, myrep, free_orbit, mycls), r);
         const uint32_t cm = d == 1 ? can_d[1] : d == 2 ? can_d[2] : can_d[0];
         if (act && ((cm >> g) & 1u)) {
-            if (COUT) reinterpret_cast<float2*>(out)[base + gi] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
-            else out[base + gi] = rows[r * kMixRow + 2 * g];
+            if (PAIR && MODE == MODE_FWD) {
+                reinterpret_cast<float2*>(out)[pb + gi] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
+            } else if (PAIR) {
+                const float2 v = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
+                out[pb + gi] = v.x;
+                out[pb + a.n3 + gi] = v.y;
+            } else if (COUT) {
+                reinterpret_cast<float2*>(out)[base + gi] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
+            } else {
+                out[base + gi] = rows[r * kMixRow + 2 * g];
+            }
         }
     });
 }

@@ -277,7 +277,10 @@ int build_host_plan(int n, HostPlan& P) {
         const int64_t sk = ((int64_t)(a / kSuperA) * (n / kSuperB + 1) + b / kSuperB) * (n / kSuperC + 1) + c / kSuperC;
         const int sub = (((a % kSuperA) / kTileA) * (kSuperB / kTileB) + (b % kSuperB) / kTileB) * (kSuperC / kTileC) +
                         (c % kSuperC) / kTileC;
-        const int64_t tk = sk * 64 + sub;
+        // class-pure tiles: the free class first, then each boundary class
+        const int64_t crank = (P.cls[o] == (uint8_t)P.free_class) ? 0 : 1 + P.cls[o];
+        const int64_t nsk = (int64_t)(n / kSuperA + 1) * (n / kSuperB + 1) * (n / kSuperC + 1);
+        const int64_t tk = (crank * nsk + sk) * 64 + sub;
         // a' fastest inside the tile
         const int64_t local = ((int64_t)(c % kTileC) * kTileB + b % kTileB) * kTileA + a % kTileA;
         items[o] = {tk * kTileMax + local, a, b, c, P.reps[o], P.cls[o]};

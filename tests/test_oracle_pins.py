@@ -275,3 +275,39 @@ def test_adjoint_identity():
     lhs = np.vdot(oracle.forward_sum_fft(x.reshape(n, n, n), n).reshape(-1), g)
     rhs = np.vdot(x, oracle.adjoint_sum_fft(g.reshape(n, n, n), n).reshape(-1))
     assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+# --- Conjugate pairs of rows for real input (used to pair real volumes) ------
+
+def _pi(n):
+    """pi(i, l, q) = (i - l, -l, q - l) mod n on flat point indices."""
+    idx = np.array(list(itertools.product(range(n), repeat=3)))
+    p = np.stack([(idx[:, 0] - idx[:, 1]) % n, (-idx[:, 1]) % n, (idx[:, 2] - idx[:, 1]) % n], 1)
+    return (p[:, 0] * n + p[:, 1]) * n + p[:, 2]
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_rows_come_in_conjugate_pairs(n):
+    """D[pi(r), :] = conj(D[r, :]): -theta_r is a W-image of theta_pi(r) modulo
+    Z^3, and T_k is W-invariant with integer-periodic exponents (Prop. 1 (iii))."""
+    D = oracle.dct_matrix(n)
+    pi = _pi(n)
+    assert (pi[pi] == np.arange(n ** 3)).all()
+    assert np.abs(D[pi] - np.conj(D)).max() < 1e-13
+
+
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_pairing_identities(n):
+    """One complex transform serves two real volumes; Re(D^-1 y) = D^-1 P(y) and
+    Re(D^H y) = D^H P(y) with P(y) = (y + conj(y o pi)) / 2."""
+    D = oracle.dct_matrix(n)
+    pi = _pi(n)
+    N = n ** 3
+    x1, x2 = RNG.standard_normal(N), RNG.standard_normal(N)
+    Y = D @ (x1 + 1j * x2)
+    assert np.abs((Y + np.conj(Y[pi])) / 2 - D @ x1).max() < 1e-12
+    assert np.abs((Y - np.conj(Y[pi])) / 2j - D @ x2).max() < 1e-12
+    y = RNG.standard_normal(N) + 1j * RNG.standard_normal(N)
+    P = (y + np.conj(y[pi])) / 2
+    assert np.abs(np.linalg.solve(D, P) - np.linalg.solve(D, y).real).max() < 1e-12
+    assert np.abs(D.conj().T @ P - (D.conj().T @ y).real).max() < 1e-12
