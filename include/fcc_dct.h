@@ -131,6 +131,36 @@ int fcc_dct_launches(const fcc_plan* plan, int which /* 0 fwd, 1 inv, 2 adj */);
 fcc_status fcc_dct_profile_enable(fcc_plan* plan, int enable);
 int fcc_dct_profile_read(fcc_plan* plan, char* names, double* ms, int* launches, int cap);
 
+/*
+ * Inverse transform that allocates nothing (the paper has no counterpart).
+ *
+ * Some callers cannot allocate device memory at the moment they need the
+ * inverse: code running inside an allocator or memory-pool callback, or a
+ * latency-critical loop in which a cudaMalloc would synchronise the device
+ * with work already running.  This entry point computes exactly what
+ * fcc_dct_inverse computes, but its complex workspace lives in one
+ * file-scope device array of FCC_STATIC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The plan (created earlier, when
+ * allocation was allowed) supplies the read-only tables; `in` and `out` are
+ * the caller's device buffers as for fcc_dct_inverse.
+ *
+ * Limits: FP32 plans only (FCC_R32, FCC_C32) whose largest volume fits the
+ * array as complex values (n^3 * 8 bytes <= FCC_STATIC_SCRATCH_BYTES, i.e.
+ * n <= 128); anything else returns FCC_ERR_UNSUPPORTED without launching.
+ * Volumes are processed one chunk at a time on `stream` only.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The array is shared by all calls and keeps
+ * the last call's contents; nothing in it needs to start at zero (every
+ * value is written before it is read).  Calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on the array and
+ * must be serialised by the caller.
+ */
+#define FCC_STATIC_SCRATCH_BYTES (16u << 20)
+fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, void* stream);
+
 /* Status of the last failing call on this host thread (FCC_OK if none). */
 fcc_status fcc_dct_last_error(void);
 const char* fcc_status_string(fcc_status status);

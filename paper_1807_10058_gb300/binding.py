@@ -20,7 +20,7 @@ EXPORTS = [
     "fcc_dct_forward_host", "fcc_dct_inverse_host", "fcc_dct_batch", "fcc_dct_points",
     "fcc_dct_in_bytes", "fcc_dct_out_bytes", "fcc_dct_launches", "fcc_dct_last_error",
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
-    "fcc_dct_profile_enable", "fcc_dct_profile_read",
+    "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static",
 ]
 
 _LIB = None
@@ -45,7 +45,7 @@ def lib():
         L.fcc_dct_plan_ragged.argtypes = [ctypes.POINTER(i32), i32, i32]
         L.fcc_dct_plan_ragged.restype = vp
         for f in ("fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint", "fcc_dct_forward_host",
-                  "fcc_dct_inverse_host"):
+                  "fcc_dct_inverse_host", "fcc_dct_inverse_static"):
             getattr(L, f).argtypes = [vp, vp, vp, vp]
             getattr(L, f).restype = i32
         L.fcc_dct_batch.argtypes = [vp]

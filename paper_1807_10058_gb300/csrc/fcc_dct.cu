@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -864,3 +865,97 @@ fcc_status fcc_dct_weyl_group(int32_t* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fcc_dct_inverse_static: the inverse with a file-scope workspace.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// The workspace of fcc_dct_inverse_static.  In host code this name is only a
+// stand-in for the symbol; kernels receive the device address obtained with
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) float2 g_static_scratch[FCC_STATIC_SCRATCH_BYTES / sizeof(float2)];
+
+constexpr int kMaxDevices = 64;
+std::atomic<float2*> g_static_addr[kMaxDevices];
+
+// Device address of g_static_scratch on the current device (looked up once).
+fcc_status static_scratch(int dev, float2** ptr) {
+    if (dev < 0 || dev >= kMaxDevices) return FCC_ERR_UNSUPPORTED;
+    float2* p = g_static_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* addr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) {
+            cudaGetLastError();
+            return FCC_ERR_CUDA;
+        }
+        p = (float2*)addr;
+        g_static_addr[dev].store(p, std::memory_order_release);
+    }
+    *ptr = p;
+    return FCC_OK;
+}
+
+// One chunk (a pair of real volumes, or one volume) at a time through the
+// static workspace, on the caller's stream only.
+fcc_status run_inverse_static(fcc_plan* p, const float* in, float* out, float2* ws, cudaStream_t st) {
+    const bool rin = is_real_in(p->dtype);
+    fcc_status s = FCC_OK;
+    int v = 0;
+    while (v < p->batch && !s) {
+        int e = v + 1;
+        while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
+        const OrderTables& t = p->tabs.at(p->orders[v]);
+        const int64_t n3 = (int64_t)t.n * t.n * t.n;
+        const float* y = in + p->offset[v] * 2;
+        float* x = out + p->offset[v] * (rin ? 1 : 2);
+        const int64_t nvol = e - v;
+        const float scale = (float)(1.0 / (double)n3);
+        if (t.n == 1) {
+            // D = [1]: copy through the workspace in chunks of whole volumes
+            const int64_t cap = FCC_STATIC_SCRATCH_BYTES / sizeof(float2);
+            for (int64_t u = 0; u < nvol && !s; u += cap) {
+                const int64_t nv = std::min(cap, nvol - u);
+                s = launch_fft<float>(t, y + 2 * u, (float*)ws, nv, 0, -1, st);
+                if (!s) s = launch_mix<float>(t, MODE_INV, false, rin, (const float*)ws, x + u * (rin ? 1 : 2), nv, 1.f, st);
+            }
+            v = e;
+            continue;
+        }
+        const int64_t npairs = (rin && nvol >= 2) ? nvol / 2 : 0;
+        for (int64_t q = 0; q < npairs && !s; ++q) {
+            s = launch_pair(false, t.n, y + q * 4 * n3, (float*)ws, 1, st);
+            if (!s) s = launch_dft3(t, -1, (const float*)ws, (float*)ws, 1, st);
+            if (!s) s = launch_mix_tiled(t, MODE_INV, false, true, (const float*)ws, x + q * 2 * n3, 1, scale, st, true);
+        }
+        for (int64_t u = 2 * npairs; u < nvol && !s; ++u) {
+            s = launch_dft3(t, -1, y + u * 2 * n3, (float*)ws, 1, st);
+            if (!s) s = launch_mix_tiled(t, MODE_INV, false, rin, (const float*)ws, x + u * n3 * (rin ? 1 : 2), 1,
+                                         scale, st);
+        }
+        v = e;
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" fcc_status fcc_dct_inverse_static(fcc_plan* p, const void* in, void* out, void* stream) {
+    if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
+    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, 1);
+    const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, 1);
+    if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
+    if (p->dtype != FCC_R32 && p->dtype != FCC_C32) return fail(FCC_ERR_UNSUPPORTED);
+    for (int n : p->orders)
+        if ((uint64_t)n * n * n * sizeof(float2) > FCC_STATIC_SCRATCH_BYTES) return fail(FCC_ERR_UNSUPPORTED);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+    float2* ws = nullptr;
+    fcc_status s = static_scratch(p->device, &ws);
+    if (!s) s = run_inverse_static(p, (const float*)in, (float*)out, ws, (cudaStream_t)stream);
+    if (cur != p->device) cudaSetDevice(cur);
+    return s == FCC_OK ? FCC_OK : fail(s);
+}
