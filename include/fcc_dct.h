@@ -27,6 +27,7 @@
  *   FCC_C64        complex double  complex double  complex double -> complex
  *   FCC_R32        float           complex float   complex float  -> float
  *   FCC_C32        complex float   complex float   complex float  -> complex
+ *   FCC_R32_*X3    as FCC_R32
  *
  * For the real dtypes the inverse returns the real part of D^{-1} y (exact
  * when y = D x for a real x) and the adjoint returns Re(D^H g), the adjoint
@@ -66,9 +67,9 @@ typedef enum {
     FCC_C64 = 1,
     FCC_R32 = 2,
     FCC_C32 = 3,
-    FCC_R32_TF32X3 = 4,
-    FCC_R32_BF16X3 = 5,
-    FCC_R32_BF16X6 = 6
+    FCC_R32_TF32X3 = 4,   /* FP32 storage; the forward orbit cores on the tensor cores (TF32, 3-term inputs) */
+    FCC_R32_BF16X3 = 5,   /* FP32 storage; the forward orbit cores on the tensor cores (BF16, 3-term inputs) */
+    FCC_R32_BF16X6 = 6    /* reserved: returns FCC_ERR_UNSUPPORTED (the core matrices are exact in BF16) */
 } fcc_dtype;
 
 /* Largest supported order n. */
@@ -160,6 +161,15 @@ int fcc_dct_profile_read(fcc_plan* plan, char* names, double* ms, int* launches,
  */
 #define FCC_STATIC_SCRATCH_BYTES (16u << 20)
 fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, void* stream);
+
+/*
+ * Wait for the device (cudaDeviceSynchronize) and report a device-side
+ * failure of the plan's earlier calls: FCC_ERR_TIMEOUT if a bounded wait of a
+ * tensor-core kernel gave up (the kernel then skipped its remaining work and
+ * released its tensor memory), FCC_ERR_CUDA if a launch or the device
+ * failed.  Clears the plan's device status word.
+ */
+fcc_status fcc_dct_check(fcc_plan* plan);
 
 /* Status of the last failing call on this host thread (FCC_OK if none). */
 fcc_status fcc_dct_last_error(void);

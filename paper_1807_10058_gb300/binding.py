@@ -20,7 +20,7 @@ EXPORTS = [
     "fcc_dct_forward_host", "fcc_dct_inverse_host", "fcc_dct_batch", "fcc_dct_points",
     "fcc_dct_in_bytes", "fcc_dct_out_bytes", "fcc_dct_launches", "fcc_dct_last_error",
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
-    "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static",
+    "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
 ]
 
 _LIB = None
@@ -55,6 +55,8 @@ def lib():
             getattr(L, f).restype = i64
         L.fcc_dct_launches.argtypes = [vp, i32]
         L.fcc_dct_launches.restype = i32
+        L.fcc_dct_check.argtypes = [vp]
+        L.fcc_dct_check.restype = i32
         L.fcc_dct_last_error.argtypes = []
         L.fcc_dct_last_error.restype = i32
         L.fcc_status_string.argtypes = [i32]
@@ -156,6 +158,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def check(self):
+        """Synchronise and raise if a device-side wait of an earlier call timed out."""
+        _check(lib().fcc_dct_check(self.handle), "fcc_dct_check")
 
     def launches(self, which=0):
         return lib().fcc_dct_launches(self.handle, which)

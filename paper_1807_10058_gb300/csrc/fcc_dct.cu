@@ -16,6 +16,7 @@
 #include "fcc_dct.h"
 #include "fft_fast.cuh"
 #include "kernels.cuh"
+#include "mix_tc.cuh"
 #include "mix_tiled.cuh"
 #include "plan.h"
 
@@ -31,6 +32,7 @@ fcc_status fail(fcc_status s) {
 }
 
 bool is_double(int dtype) { return dtype == FCC_R64 || dtype == FCC_C64; }
+bool is_tc(int dtype) { return dtype == FCC_R32_TF32X3 || dtype == FCC_R32_BF16X3; }
 bool is_real_in(int dtype) { return dtype != FCC_C64 && dtype != FCC_C32; }
 
 // Device copy of one order's tables.
@@ -54,6 +56,9 @@ struct OrderTables {
     uint8_t* tile_cls = nullptr;
     uint8_t* tile_pb = nullptr;
     uint8_t* tile_pc = nullptr;
+    int free_tiles = 0;
+    // tensor-core dtypes: the A operand image of the free-orbit forward core
+    void* tc_a_image = nullptr;
 };
 
 constexpr int kMaxStreams = 4;
@@ -79,8 +84,11 @@ struct fcc_plan {
     int64_t chunk_bytes = 32ll << 20;
     int nstreams = 2;
     bool pairing = true;             // real dtypes: two volumes per complex transform
+    int num_sms = 1;
+    int* d_status = nullptr;         // device-side wait timeouts (tensor-core kernels)
     cudaStream_t streams[kMaxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t bnd_ev = nullptr;    // boundary tiles done (forward)
     cudaEvent_t join_ev[kMaxStreams] = {};
     // per-kernel timing (fcc_dct_profile_enable)
     bool profiling = false;
@@ -164,6 +172,14 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     if ((s = upload(p, &t.tw, twv.data(), twv.size() * sizeof(T)))) return s;
     t.free_class = hp.free_class;
     t.ntiles = (int)hp.tile_off.size() - 1;
+    t.free_tiles = hp.free_tiles;
+    if (is_tc(p->dtype) && hp.free_class >= 0) {
+        std::vector<unsigned char> img;
+        const bool ok = p->dtype == FCC_R32_BF16X3 ? build_tc_a_image<0>(hp.classes[hp.free_class].fwd.data(), img)
+                                                   : build_tc_a_image<1>(hp.classes[hp.free_class].fwd.data(), img);
+        if (!ok) return FCC_ERR_UNSUPPORTED;
+        if ((s = upload(p, &t.tc_a_image, img.data(), img.size()))) return s;
+    }
     if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_cls, hp.tile_cls.data(), hp.tile_cls.size()))) return s;
@@ -216,6 +232,7 @@ void release(fcc_plan* p) {
         if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->bnd_ev) cudaEventDestroy(p->bnd_ev);
     for (auto e : p->event_pool) cudaEventDestroy(e);
     cudaSetDevice(cur);
     delete p;
@@ -223,7 +240,7 @@ void release(fcc_plan* p) {
 
 fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
     if (dtype < FCC_R64 || dtype > FCC_R32_BF16X6) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
-    if (dtype > FCC_C32) { fail(FCC_ERR_UNSUPPORTED); return nullptr; }
+    if (dtype == FCC_R32_BF16X6) { fail(FCC_ERR_UNSUPPORTED); return nullptr; }
     if (orders.empty()) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     for (int n : orders)
         if (n < 1 || n > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
@@ -243,7 +260,12 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         maxpts = std::max(maxpts, n3);
     }
     p->points = off;
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (p->num_sms < 1) p->num_sms = 1;
     fcc_status s = upload_group();
+    if (s == FCC_OK && (s = dev_alloc(p, (void**)&p->d_status, sizeof(int))) == FCC_OK &&
+        cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+        s = FCC_ERR_CUDA;
     for (int n : orders) {
         if (s != FCC_OK) break;
         if (p->tabs.count(n)) continue;
@@ -261,6 +283,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
                 s = FCC_ERR_CUDA;
         }
         if (s == FCC_OK && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
+        if (s == FCC_OK && cudaEventCreateWithFlags(&p->bnd_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
     }
     if (s == FCC_OK) {
         // workspace for inverse / adjoint: one chunk per internal stream
@@ -435,8 +458,27 @@ fcc_status launch_fast_fft(int n, bool slab, int sign, const float2* in, float2*
     }
 }
 
+// Dynamic shared memory limits of every instantiation of mix_tiled_kernel
+// (set once per process, before the first launch of any of them).
+void set_mix_tiled_attributes() {
+    static bool attr = false;
+    if (attr) return;
+    const int lim = 200 * 1024;
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    attr = true;
+}
+
+// which: 0 = every tile, 1 = free tiles only, 2 = boundary tiles only
 fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
-                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false) {
+                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false, int which = 0) {
     TiledMixArgs a;
     a.tile_off = t.tile_off;
     a.reps = t.tile_reps;
@@ -462,48 +504,44 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
     a.scale = scale;
     if (t.n_classes > kMaxClasses) return FCC_ERR_UNSUPPORTED;
     const size_t smem = mix_tiled_smem(t.n);
-    static bool attr = false;
-    if (!attr) {
-        const int lim = 200 * 1024;
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        attr = true;
-    }
+    set_mix_tiled_attributes();
     static const char* names[3] = {"mix_tiled_fwd", "mix_tiled_inv", "mix_tiled_adj"};
-    for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
-        const int64_t nv = std::min<int64_t>(65535, nvol - v0);
-        dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
-        const int nt = t.ntiles;
-        if (pair) {
-            // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes;
-            // inverse / adjoint: compact complex -> real volumes 2p, 2p+1
-            const float* src = in + v0 * a.n3 * 2;
-            float* dst = out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
+    // two launches: free tiles (cores in constant memory) and boundary tiles
+    // (one class core per warp staged in shared memory)
+    const int ranges[2][2] = {{0, t.free_tiles}, {t.free_tiles, t.ntiles}};
+    for (int rg = 0; rg < 2; ++rg) {
+        const int tile0 = ranges[rg][0], tile1 = ranges[rg][1];
+        if (tile1 <= tile0 || (which == 1 && rg == 1) || (which == 2 && rg == 0)) continue;
+        const size_t sm = rg == 0 ? smem : mix_tiled_smem_core(t.n);
+        const int core = rg == 1;
+        for (int64_t v0 = 0; v0 < nvol; v0 += 65535) {
+            const int64_t nv = std::min<int64_t>(65535, nvol - v0);
+            dim3 grid((unsigned)((tile1 - tile0 + kMixWarps - 1) / kMixWarps), (unsigned)nv);
+            const int nt = tile1;
+            if (pair) {
+                // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes;
+                // inverse / adjoint: compact complex -> real volumes 2p, 2p+1
+                const float* src = in + v0 * a.n3 * 2;
+                float* dst = out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
+                ProfScope ps(names[mode], st);
+                if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                continue;
+            }
+            const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
+            float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
             ProfScope ps(names[mode], st);
-            if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            continue;
-        }
-        const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
-        float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
-        ProfScope ps(names[mode], st);
-        if (mode == MODE_FWD) {
-            if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-        } else if (mode == MODE_INV) {
-            if (real_out) mix_tiled_kernel<MODE_INV, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            else mix_tiled_kernel<MODE_INV, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-        } else {
-            if (real_out) mix_tiled_kernel<MODE_ADJ, false, true><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
-            else mix_tiled_kernel<MODE_ADJ, false, false><<<grid, kMixThreads, smem, st>>>(src, dst, a, nt);
+            if (mode == MODE_FWD) {
+                if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+            } else if (mode == MODE_INV) {
+                if (real_out) mix_tiled_kernel<MODE_INV, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                else mix_tiled_kernel<MODE_INV, false, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+            } else {
+                if (real_out) mix_tiled_kernel<MODE_ADJ, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                else mix_tiled_kernel<MODE_ADJ, false, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+            }
         }
     }
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
@@ -558,6 +596,67 @@ fcc_status launch_pair(bool split, int n, const float* in, float* out, int64_t n
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
+// Forward mixing of `np` pairs of real volumes with the orbit core on the
+// tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
+fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
+                               cudaStream_t st) {
+    TiledMixArgs a;
+    a.tile_off = t.tile_off;
+    a.reps = t.tile_reps;
+    a.cls = t.tile_cls;
+    a.permb = t.tile_pb;
+    a.permc = t.tile_pc;
+    a.mats = (const float*)t.mat[MODE_FWD];
+    a.wrap = t.wrap;
+    a.canon_mask = t.canon_mask;
+    a.phase = (const float2*)t.phase;
+    a.n = t.n;
+    for (int g = 0; g < 24; ++g) {
+        const int n = t.n;
+        for (int j = 0; j < 3; ++j)
+            a.lin[g][j] = wc::K::t.m[g][j] * n * n + wc::K::t.m[g][3 + j] * n + wc::K::t.m[g][6 + j];
+        a.lin[g][3] = -n * (wc::K::t.fw[g][0] * n * n + wc::K::t.fw[g][1] * n + wc::K::t.fw[g][2]);
+    }
+    a.ncls = t.n_classes;
+    a.free_class = t.free_class;
+    a.n3 = (int64_t)t.n * t.n * t.n;
+    a.scale = 1.f;
+    const bool bf16 = p->dtype == FCC_R32_BF16X3;
+    const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
+    set_mix_tiled_attributes();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<0>::smem);
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<1>::smem);
+        attr = true;
+    }
+    for (int64_t v0 = 0; v0 < np; v0 += 65535) {
+        const int64_t nv = std::min<int64_t>(65535, np - v0);
+        const float* src = in + v0 * a.n3 * 2;
+        float* dst = out + v0 * a.n3 * 4;
+        if (t.free_tiles > 0 && t.tc_a_image) {
+            const int ngroups = (t.free_tiles + 3) / 4;
+            const int per_sm = bf16 ? 3 : 1;
+            const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
+            dim3 grid((unsigned)gx, (unsigned)nv);
+            ProfScope ps("mix_tc_fwd", st);
+            if (bf16)
+                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
+                                                                          (const uint4*)t.tc_a_image, p->d_status);
+            else
+                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
+                                                                          (const uint4*)t.tc_a_image, p->d_status);
+        }
+        if (!t.tc_a_image) {   // no free orbits at this order: every tile is a boundary tile
+            dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
+            ProfScope ps("mix_tiled_fwd", st);
+            mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, mix_tiled_smem_core(t.n), st>>>(
+                src, dst, a, t.ntiles, 0, 1);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
 int64_t chunk_vols(const fcc_plan* p, int n) {
     const int64_t n3 = (int64_t)n * n * n;
     return std::max<int64_t>(1, p->chunk_bytes / (n3 * 8));
@@ -580,13 +679,31 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     const bool pairing = rin && p->pairing && nvol >= 2;
     const int64_t npairs = pairing ? nvol / 2 : 0;
     const int64_t cp = cv;   // pairs per chunk: one complex volume of intermediate per pair
+    // forward: the boundary (non-free) tiles of every pair in one launch on the
+    // first stream, before the chunks' DFT passes (each chunk waits for it)
+    const bool split_boundary = which == 0 && npairs > 0 && t.free_tiles > 0 && t.ntiles > t.free_tiles;
+    if (split_boundary) {
+        s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, npairs, 1.f, p->streams[0], true, 2);
+        if (!s && cudaEventRecord(p->bnd_ev, p->streams[0]) != cudaSuccess) s = FCC_ERR_CUDA;
+        for (int i = 1; i < ns && !s; ++i)
+            if (cudaStreamWaitEvent(p->streams[i], p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
+    }
     for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
         const int64_t np = std::min(cp, npairs - p0);
         cudaStream_t ss = p->streams[c % ns];
         if (which == 0) {
             const float* x = in + 2 * p0 * n3;
             float* y = out + 2 * p0 * n3 * 2;
-            s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true);
+            const int part = split_boundary ? 1 : 0;
+            if (is_tc(p->dtype) && t.tc_a_image) {
+                s = launch_mix_tc_pairs(p, t, x, y, np, ss);
+                if (!s && !split_boundary && t.ntiles > t.free_tiles)
+                    s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, 2);
+            } else if (is_tc(p->dtype)) {
+                s = launch_mix_tc_pairs(p, t, x, y, np, ss);
+            } else {
+                s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, part);
+            }
             if (!s) s = launch_dft3(t, +1, y, y, np, ss, 2 * n3);
             if (!s) s = launch_pair(true, t.n, nullptr, y, np, ss);
         } else {
@@ -757,13 +874,17 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         if (!is_double(p->dtype) && n > 1) {
             const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
             const int dft = has_fast_fft(n) ? 2 : 3;
+            const OrderTables& tb = p->tabs.at(n);
+            const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
             const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
             const int64_t npairs = pairing ? nv / 2 : 0;
             const int64_t pchunks = (npairs + cv - 1) / cv;
             const int64_t dft_per_pchunk = has_fast_fft(n) ? 2 : 3 * cv;   // generic passes go volume by volume
-            total += (int)(pchunks * (2 + dft_per_pchunk));
+            const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
+            if (split_b) total += 1 + (int)(pchunks * (1 + 1 + dft_per_pchunk));
+            else total += (int)(pchunks * (mixl + 1 + dft_per_pchunk));
             const int64_t rest = nv - 2 * npairs;
-            total += (int)(((rest + cv - 1) / cv) * (1 + dft));
+            total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
         } else if (which == 0) total += mix + 3;
         else {
             const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
@@ -808,6 +929,24 @@ int fcc_dct_profile_read(fcc_plan* p, char* names, double* ms, int* launches, in
         if (launches) launches[k] = cnt[k];
     }
     return (int)kinds.size();
+}
+
+fcc_status fcc_dct_check(fcc_plan* p) {
+    if (!p) return fail(FCC_ERR_INVALID_ARG);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    int st = 0;
+    fcc_status s = FCC_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        s = FCC_ERR_CUDA;
+    } else if (st != 0) {
+        cudaMemset(p->d_status, 0, sizeof(int));
+        s = FCC_ERR_TIMEOUT;
+    }
+    if (cur != p->device) cudaSetDevice(cur);
+    return s == FCC_OK ? FCC_OK : fail(s);
 }
 
 fcc_status fcc_dct_last_error(void) { return g_last; }

@@ -129,13 +129,13 @@ __device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
 template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
 __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
                                                                    float* __restrict__ out, const TiledMixArgs a,
-                                                                   int ntiles) {
+                                                                   int ntiles, int tile0 = 0, int core_in_smem = 0) {
     constexpr bool CIN = (MODE != MODE_FWD) || !RIN || PAIR;    // complex values in the core
     constexpr bool COUT = (MODE == MODE_FWD) || !ROUT || PAIR;  // complex values out of the core
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
-    const int tile = blockIdx.x * kMixWarps + warp;
+    const int tile = tile0 + blockIdx.x * kMixWarps + warp;
     if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
     const int64_t base = (int64_t)blockIdx.y * a.n3;   // unpaired volume offset (values)
     const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;  // paired: first volume of the pair
@@ -188,6 +188,15 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
             });
         }
     }
+    // boundary tiles (one class per tile): all 32 lanes stage the class core
+    if (core_in_smem) {
+        const int tcls = __shfl_sync(0xffffffffu, mycls, 0);
+        if (tcls != a.free_class) {
+            float* Ms = reinterpret_cast<float*>(smem_raw) + kMixWarps * 32 * kMixRow + warp * 1152;
+            const float4* src = reinterpret_cast<const float4*>(a.mats + (size_t)tcls * 1152);
+            for (int e = lane; e < 1152 / 4; e += 32) reinterpret_cast<float4*>(Ms)[e] = __ldg(src + e);
+        }
+    }
     __syncwarp();
     // ---- core: lane = orbit, in place in its own row
     if (act) {
@@ -238,19 +247,21 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
                 }
             });
         } else {
-            // rare (orbits on the alcove boundary): class core from global memory
-            const float* M = a.mats + (size_t)mycls * 1152;
+            // orbits on the alcove boundary: the tile's class core (staged in
+            // this warp's shared-memory slot above, when the launch provides one)
+            const float* M = core_in_smem ? reinterpret_cast<const float*>(smem_raw) + kMixWarps * 32 * kMixRow + warp * 1152
+                                          : a.mats + (size_t)mycls * 1152;
 #pragma unroll 1
             for (int g = 0; g < 24; ++g) {
                 float ar = 0.f, ai = 0.f;
 #pragma unroll
                 for (int h = 0; h < 24; ++h) {
-                    const float mr = __ldg(M + 2 * (g * 24 + h)), mi = __ldg(M + 2 * (g * 24 + h) + 1);
-                    ar = fmaf(mr, xr[h], ar);
-                    ai = fmaf(mi, xr[h], ai);
+                    const float2 m = *reinterpret_cast<const float2*>(M + 2 * (g * 24 + h));
+                    ar = fmaf(m.x, xr[h], ar);
+                    ai = fmaf(m.y, xr[h], ai);
                     if (CIN) {
-                        ar = fmaf(-mi, xi[h], ar);
-                        ai = fmaf(mr, xi[h], ai);
+                        ar = fmaf(-m.y, xi[h], ar);
+                        ai = fmaf(m.x, xi[h], ai);
                     }
                 }
                 if (MODE == MODE_FWD) {
@@ -295,5 +306,7 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
 }
 
 inline size_t mix_tiled_smem(int) { return (size_t)kMixWarps * 32 * kMixRow * 4; }
+// launches over boundary tiles also stage one class core per warp
+inline size_t mix_tiled_smem_core(int n) { return mix_tiled_smem(n) + (size_t)kMixWarps * 1152 * 4; }
 
 }  // namespace fcc

@@ -268,7 +268,7 @@ int build_host_plan(int n, HostPlan& P) {
     for (int c = 0; c < ncls; ++c) P.orbits_per_class_max = std::max(P.orbits_per_class_max, P.class_count[c]);
 
     // Tiles.
-    struct Item { int64_t key; int a, b, c; uint32_t rep; uint8_t cls; };
+    struct Item { int64_t key; int a, b, c; uint32_t rep; uint8_t cls; int64_t local = 0; };
     std::vector<Item> items(P.reps.size());
     for (size_t o = 0; o < P.reps.size(); ++o) {
         const int k1 = P.reps[o] & 1023, k2 = (P.reps[o] >> 10) & 1023, k3 = (P.reps[o] >> 20) & 1023;
@@ -277,15 +277,32 @@ int build_host_plan(int n, HostPlan& P) {
         const int64_t sk = ((int64_t)(a / kSuperA) * (n / kSuperB + 1) + b / kSuperB) * (n / kSuperC + 1) + c / kSuperC;
         const int sub = (((a % kSuperA) / kTileA) * (kSuperB / kTileB) + (b % kSuperB) / kTileB) * (kSuperC / kTileC) +
                         (c % kSuperC) / kTileC;
-        // class-pure tiles: the free class first, then each boundary class
+        // class-pure tiles: the free class first (boxes), then each boundary
+        // class packed in runs of kTileMax along (a', b', c') (boundary orbits
+        // lie on faces of the alcove, where boxes would be mostly empty)
         const int64_t crank = (P.cls[o] == (uint8_t)P.free_class) ? 0 : 1 + P.cls[o];
         const int64_t nsk = (int64_t)(n / kSuperA + 1) * (n / kSuperB + 1) * (n / kSuperC + 1);
-        const int64_t tk = (crank * nsk + sk) * 64 + sub;
+        int64_t tk = (crank * nsk + sk) * 64 + sub;
+        if (crank > 0) tk = (crank * nsk) * 64;   // one key per class; split into runs below
         // a' fastest inside the tile
-        const int64_t local = ((int64_t)(c % kTileC) * kTileB + b % kTileB) * kTileA + a % kTileA;
-        items[o] = {tk * kTileMax + local, a, b, c, P.reps[o], P.cls[o]};
+        int64_t local = ((int64_t)(c % kTileC) * kTileB + b % kTileB) * kTileA + a % kTileA;
+        if (crank > 0) local = ((int64_t)a * (n + 1) + b) * (n + 1) + c;   // order inside the class
+        items[o] = {tk, a, b, c, P.reps[o], P.cls[o]};
+        items[o].local = local;
     }
-    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.key < y.key; });
+    std::sort(items.begin(), items.end(),
+              [](const Item& x, const Item& y) { return x.key != y.key ? x.key < y.key : x.local < y.local; });
+    // boundary classes: consecutive runs of kTileMax orbits become tiles
+    {
+        size_t i0 = 0;
+        while (i0 < items.size()) {
+            size_t e = i0;
+            while (e < items.size() && items[e].key == items[i0].key) ++e;
+            if (items[i0].cls != (uint8_t)P.free_class)
+                for (size_t t = i0; t < e; ++t) items[t].key += (int64_t)((t - i0) / kTileMax) + 1;
+            i0 = e;
+        }
+    }
     P.tile_off.clear();
     P.tile_reps.resize(items.size());
     P.tile_cls.resize(items.size());
@@ -294,8 +311,8 @@ int build_host_plan(int n, HostPlan& P) {
     size_t i = 0;
     while (i < items.size()) {
         size_t e = i;
-        const int64_t tk = items[i].key / kTileMax;
-        while (e < items.size() && items[e].key / kTileMax == tk) ++e;
+        const int64_t tk = items[i].key;
+        while (e < items.size() && items[e].key == tk) ++e;
         P.tile_off.push_back((int32_t)i);
         P.max_tile = std::max(P.max_tile, (int)(e - i));
         std::vector<int> ord(e - i);
@@ -323,6 +340,9 @@ int build_host_plan(int n, HostPlan& P) {
         i = e;
     }
     P.tile_off.push_back((int32_t)items.size());
+    P.free_tiles = 0;
+    for (size_t t = 0; t + 1 < P.tile_off.size(); ++t)
+        if ((int)P.tile_cls[P.tile_off[t]] == P.free_class) P.free_tiles = (int)t + 1;
     return 0;
 }
 

@@ -80,6 +80,7 @@ struct HostPlan {
     std::vector<uint8_t> tile_perm_b;
     std::vector<uint8_t> tile_perm_c;
     int max_tile = 0;
+    int free_tiles = 0;              // tiles [0, free_tiles) hold free orbits only
 };
 
 constexpr int kTileA = 4, kTileB = 4, kTileC = 2;   // one warp per tile

@@ -171,5 +171,63 @@ def test_unsupported_order_reports_status():
         binding.Plan(37, 1, "r32")
     assert e.value.status == binding.FCC_ERR_UNSUPPORTED
     with pytest.raises(binding.FccError) as e:
-        binding.Plan(8, 1, "r32_tf32x3")
+        binding.Plan(8, 1, "r32_bf16x6")
     assert e.value.status == binding.FCC_ERR_UNSUPPORTED
+
+
+# --- tensor-core form: the forward orbit cores on tcgen05 ----------------------
+
+TC_TOL = 1e-6   # relative L2 against the FP64 oracle
+
+
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32_tf32x3"])
+@pytest.mark.parametrize("n,batch", [(2, 2), (5, 3), (8, 2), (16, 4), (24, 2), (64, 2)])
+def test_tensor_core_forward_full_volumes(dtype, n, batch):
+    x = inputs.smoothed_noise(n, batch, seed=5).astype(np.float32)
+    ref = oracle.forward_sum_fft(x.astype(np.float64), n)
+    with binding.Plan(n, batch, dtype) as p:
+        y = host(p.forward(dev(x, np.float32)), x.shape)
+        xi = host(p.inverse(dev(ref, np.complex64)), x.shape)
+        p.check()
+    assert rel(y, ref) < TC_TOL, rel(y, ref)
+    assert rel(xi, x) < 4e-5
+
+
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32_tf32x3"])
+def test_tensor_core_forward_order_128_sampled(dtype):
+    n, batch = 128, 4
+    checked = [0, 3]
+    x, hv = _full_size(n, batch, checked, seed=21, maker=inputs.phantom)
+    rng = np.random.default_rng(3)
+    with binding.Plan(n, batch, dtype) as p, binding.Plan(n, batch, "r32") as q:
+        y = p.forward(x)
+        y32 = q.forward(x)
+        p.check()
+        for v in checked:
+            rows = rng.integers(0, n ** 3, size=24)
+            ref = oracle.forward_rows(hv[v].astype(np.float32).astype(np.float64), n, rows)
+            got = y[v * n ** 3 + torch.from_numpy(rows).to(DEV)].cpu().numpy()
+            rms = torch.sqrt(torch.mean(torch.abs(y[v * n ** 3:(v + 1) * n ** 3]) ** 2)).item()
+            est = np.sqrt(np.mean(np.abs(got - ref) ** 2)) / rms
+            assert est < TC_TOL, (v, est)
+        # the tensor-core and SIMT forms agree to FP32 rounding everywhere
+        d = (torch.linalg.vector_norm(y - y32) / torch.linalg.vector_norm(y32)).item()
+        assert d < TC_TOL, d
+
+
+def test_tensor_core_form_in_a_fresh_process():
+    """The tensor-core plan is usable as the first thing a process does (no
+    state left behind by other paths)."""
+    import subprocess
+    import sys
+    code = ("import torch, sys; sys.path.insert(0, '.');"
+            "from paper_1807_10058_gb300 import binding;"
+            "p = binding.Plan(64, 4, 'r32_bf16x3'); q = binding.Plan(64, 4, 'r32');"
+            "x = torch.rand(4 * 64 ** 3, device='cuda');"
+            "a = p.forward(x); b = q.forward(x); p.check();"
+            "print((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item())")
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert float(out.stdout.strip().splitlines()[-1]) < 1e-6
