@@ -18,6 +18,7 @@
 #include "kernels.cuh"
 #include "mix_tc.cuh"
 #include "mix_tiled.cuh"
+#include "pair.cuh"
 #include "plan.h"
 
 using namespace fcc;
@@ -59,6 +60,9 @@ struct OrderTables {
     int free_tiles = 0;
     // tensor-core dtypes: the A operand image of the free-orbit forward core
     void* tc_a_image = nullptr;
+    // ragged plans: point offsets of this order's volumes (device), when all even
+    int64_t* voff = nullptr;
+    int nvoff = 0;
 };
 
 constexpr int kMaxStreams = 4;
@@ -84,6 +88,7 @@ struct fcc_plan {
     int64_t chunk_bytes = 32ll << 20;
     int nstreams = 2;
     bool pairing = true;             // real dtypes: two volumes per complex transform
+    bool ragged_fast = true;         // ragged FP32 forward: per-order launches over offset tables
     int num_sms = 1;
     int* d_status = nullptr;         // device-side wait timeouts (tensor-core kernels)
     cudaStream_t streams[kMaxStreams] = {};
@@ -273,10 +278,27 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         s = is_double(dtype) ? build_tables<double>(p, n, t) : build_tables<float>(p, n, t);
         p->tabs[n] = t;
     }
+    if (s == FCC_OK && !p->uniform && !is_double(dtype)) {
+        // ragged: per order, the point offsets of its volumes (all even, so that
+        // 16-byte accesses of the DFT passes stay aligned)
+        std::map<int, std::vector<int64_t>> offs;
+        bool even = true;
+        for (size_t v = 0; v < orders.size(); ++v) {
+            offs[orders[v]].push_back(p->offset[v]);
+            even = even && (p->offset[v] % 2 == 0);
+        }
+        if (even)
+            for (auto& kv : offs) {
+                OrderTables& t = p->tabs[kv.first];
+                t.nvoff = (int)kv.second.size();
+                if ((s = upload(p, (void**)&t.voff, kv.second.data(), kv.second.size() * sizeof(int64_t)))) break;
+            }
+    }
     if (s == FCC_OK) {
         if (const char* e = std::getenv("FCC_CHUNK_MB")) p->chunk_bytes = std::max(1, std::atoi(e)) * (1ll << 20);
         if (const char* e = std::getenv("FCC_STREAMS")) p->nstreams = std::min(kMaxStreams, std::max(1, std::atoi(e)));
         if (const char* e = std::getenv("FCC_PAIRING")) p->pairing = std::atoi(e) != 0;
+        if (const char* e = std::getenv("FCC_RAGGED_GROUPED")) p->ragged_fast = std::atoi(e) != 0;
         for (int i = 0; i < p->nstreams && s == FCC_OK; ++i) {
             if (cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
@@ -408,54 +430,11 @@ fcc_status launch_mix(const OrderTables& t, int mode, bool real_in, bool real_ou
 
 // --- FP32 fast path -------------------------------------------------------
 
-template <int N>
-fcc_status launch_fast_fft_n(bool slab, int sign, const float2* in, float2* out, int64_t nvol, const float2* tw,
-                             int64_t vstride, cudaStream_t st) {
-    using L = FastLayout<N>;
-    if (slab) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(fft_slab_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
-            cudaFuncSetAttribute(fft_slab_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
-            attr = true;
-        }
-        ProfScope ps("fft_slab", st);
-        const unsigned grid = (unsigned)(nvol * N);
-        if (sign > 0) fft_slab_kernel<N, 1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw, vstride);
-        else fft_slab_kernel<N, -1><<<grid, kSlabThreads, L::slab_smem, st>>>(in, out, tw, vstride);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(fft_pencil_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-            cudaFuncSetAttribute(fft_pencil_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-            attr = true;
-        }
-        constexpr int CPB = kFastWarps * L::PPW * 2;
-        const unsigned grid = (unsigned)(nvol * N * ((N + CPB - 1) / CPB));
-        ProfScope ps("fft_pencil", st);
-        if (sign > 0) fft_pencil_kernel<N, 1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
-        else fft_pencil_kernel<N, -1><<<grid, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
-    }
-    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
-}
-
-bool has_fast_fft(int n) {
-    switch (n) {
-        case 128: case 96: case 64: case 32: case 16: return true;
-        default: return false;
-    }
-}
-
-fcc_status launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
-                           const float2* tw, int64_t vstride, cudaStream_t st) {
-    switch (n) {
-        case 128: return launch_fast_fft_n<128>(slab, sign, in, out, nvol, tw, vstride, st);
-        case 96: return launch_fast_fft_n<96>(slab, sign, in, out, nvol, tw, vstride, st);
-        case 64: return launch_fast_fft_n<64>(slab, sign, in, out, nvol, tw, vstride, st);
-        case 32: return launch_fast_fft_n<32>(slab, sign, in, out, nvol, tw, vstride, st);
-        case 16: return launch_fast_fft_n<16>(slab, sign, in, out, nvol, tw, vstride, st);
-        default: return FCC_ERR_UNSUPPORTED;
-    }
+// fast DFT passes (fft_fast.cu), wrapped with the per-kernel timing scope
+fcc_status fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol, const float2* tw,
+                    int64_t vstride, cudaStream_t st, const int64_t* voff = nullptr) {
+    ProfScope ps(slab ? "fft_slab" : "fft_pencil", st);
+    return launch_fast_fft(n, slab, sign, in, out, nvol, tw, vstride, voff, st) == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
 // Dynamic shared memory limits of every instantiation of mix_tiled_kernel
@@ -478,7 +457,8 @@ void set_mix_tiled_attributes() {
 
 // which: 0 = every tile, 1 = free tiles only, 2 = boundary tiles only
 fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
-                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false, int which = 0) {
+                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false, int which = 0,
+                            const int64_t* voff = nullptr) {
     TiledMixArgs a;
     a.tile_off = t.tile_off;
     a.reps = t.tile_reps;
@@ -532,7 +512,10 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
             const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
             float* dst = out + v0 * a.n3 * ((mode != MODE_FWD && real_out) ? 1 : 2);
             ProfScope ps(names[mode], st);
-            if (mode == MODE_FWD) {
+            if (voff) {   // ragged: volumes at the listed point offsets (forward only)
+                if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, sm, st>>>(in, out, a, nt, tile0, core, voff + v0);
+                else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kMixThreads, sm, st>>>(in, out, a, nt, tile0, core, voff + v0);
+            } else if (mode == MODE_FWD) {
                 if (real_in) mix_tiled_kernel<MODE_FWD, true, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
                 else mix_tiled_kernel<MODE_FWD, false, false><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
             } else if (mode == MODE_INV) {
@@ -554,15 +537,18 @@ fcc_status launch_dft3(const OrderTables& t, int sign, const float* in, float* o
                        int64_t vstride = 0) {
     const int64_t n3 = (int64_t)t.n * t.n * t.n;
     if (vstride == 0) vstride = n3;
-    if (has_fast_fft(t.n)) {
+    // the fast passes move 16-byte pairs of complex values: they need 16-byte
+    // aligned volume bases (ragged batches can place a volume at an odd offset)
+    const bool aligned = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0 && vstride % 2 == 0;
+    if (has_fast_fft(t.n) && aligned) {
         const float2* tw = (const float2*)t.tw;
         fcc_status s;
         if (sign > 0) {
-            if ((s = launch_fast_fft(t.n, true, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
-            return launch_fast_fft(t.n, false, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
+            if ((s = fast_fft(t.n, true, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
+            return fast_fft(t.n, false, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
         }
-        if ((s = launch_fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
-        return launch_fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
+        if ((s = fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
+        return fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
     }
     // generic passes work on contiguous volumes: one launch set per volume when strided
     fcc_status s = FCC_OK;
@@ -740,6 +726,38 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     return s;
 }
 
+// Ragged FP32 forward: per distinct order, one mixing launch and one slab and
+// one pencil launch over that order's volumes (device table of point
+// offsets), the orders spread over the internal streams.
+bool ragged_fast_ok(const fcc_plan* p, int which) {
+    if (p->uniform || which != 0 || is_double(p->dtype)) return false;
+    for (const auto& kv : p->tabs)
+        if (!kv.second.voff || !has_fast_fft(kv.first)) return false;
+    return true;
+}
+
+fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_t st) {
+    const bool rin = is_real_in(p->dtype);
+    const int ns = p->nstreams;
+    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    fcc_status s = FCC_OK;
+    int c = 0;
+    for (auto it = p->tabs.begin(); it != p->tabs.end() && !s; ++it, ++c) {
+        const OrderTables& t = it->second;
+        cudaStream_t ss = p->streams[c % ns];
+        s = launch_mix_tiled(t, MODE_FWD, rin, false, in, out, t.nvoff, 1.f, ss, false, 0, t.voff);
+        if (!s) s = fast_fft(t.n, true, +1, (const float2*)out, (float2*)out, t.nvoff, (const float2*)t.tw, 0, ss, t.voff);
+        if (!s) s = fast_fft(t.n, false, +1, (const float2*)out, (float2*)out, t.nvoff, (const float2*)t.tw, 0, ss, t.voff);
+    }
+    for (int i = 0; i < ns; ++i) {
+        if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    return s;
+}
+
 // Run a group of `nvol` consecutive volumes of the same order.
 template <typename T>
 fcc_status run_group(fcc_plan* p, int which, const OrderTables& t, const T* in, T* out, int64_t nvol,
@@ -789,6 +807,8 @@ template <typename T>
 fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t st) {
     const T* in = (const T*)vin;
     T* out = (T*)vout;
+    if (sizeof(T) == 4 && p->ragged_fast && ragged_fast_ok(p, which))
+        return run_ragged_fast(p, (const float*)vin, (float*)vout, st);
     const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
     fcc_status s = FCC_OK;
@@ -863,6 +883,13 @@ int64_t fcc_dct_out_bytes(const fcc_plan* p) { return p ? out_bytes(p, 0) : 0; }
 int fcc_dct_launches(const fcc_plan* p, int which) {
     if (!p) return 0;
     int total = 0;
+    if (!is_double(p->dtype) && p->ragged_fast && ragged_fast_ok(p, which)) {
+        for (const auto& kv : p->tabs) {
+            const OrderTables& t = kv.second;
+            total += (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0) + 2;
+        }
+        return total;
+    }
     int v = 0;
     while (v < p->batch) {
         int e = v + 1;

@@ -1,0 +1,62 @@
+// Instantiations and host launchers of the fast DFT passes (fft_fast.cuh),
+// kept in their own translation unit so they compile in parallel with the
+// rest of the library.
+#include "fft_fast.cuh"
+
+namespace fcc {
+
+namespace {
+
+template <int N>
+cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t nvol, const float2* tw,
+                     int64_t vstride, const int64_t* voff, cudaStream_t st) {
+    using L = FastLayout<N>;
+    // 16-byte accesses: refuse (without launching) bases that are not aligned
+    if (((((uintptr_t)in) | ((uintptr_t)out)) & 15u) != 0 || (!voff && vstride % 2 != 0)) return cudaErrorMisalignedAddress;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(fft_slab_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
+        cudaFuncSetAttribute(fft_slab_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
+        cudaFuncSetAttribute(fft_pencil_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        cudaFuncSetAttribute(fft_pencil_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        attr = true;
+    }
+    if (slab) {
+        const int64_t g = nvol * N;
+        if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if (sign > 0) fft_slab_kernel<N, 1><<<(unsigned)g, L::SLAB_THREADS, L::slab_smem, st>>>(in, out, tw, vstride, voff);
+        else fft_slab_kernel<N, -1><<<(unsigned)g, L::SLAB_THREADS, L::slab_smem, st>>>(in, out, tw, vstride, voff);
+    } else {
+        const int64_t g = nvol * N * ((N + L::CPB - 1) / L::CPB);
+        if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if (sign > 0) fft_pencil_kernel<N, 1><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride, voff);
+        else fft_pencil_kernel<N, -1><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride, voff);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool has_fast_fft(int n) {
+    switch (n) {
+        case 128: case 96: case 88: case 80: case 72: case 64: case 56: case 48: case 40: case 32: case 24:
+        case 16: case 8:
+            return true;
+        default:
+            return false;
+    }
+}
+
+cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
+                            const float2* tw, int64_t vstride, const int64_t* voff, cudaStream_t st) {
+    switch (n) {
+#define FCC_CASE(NN) case NN: return launch_n<NN>(slab, sign, in, out, nvol, tw, vstride, voff, st);
+        FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
+        FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
+#undef FCC_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fcc

@@ -129,7 +129,8 @@ __device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
 template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
 __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
                                                                    float* __restrict__ out, const TiledMixArgs a,
-                                                                   int ntiles, int tile0 = 0, int core_in_smem = 0) {
+                                                                   int ntiles, int tile0 = 0, int core_in_smem = 0,
+                                                                   const int64_t* voff = nullptr) {
     constexpr bool CIN = (MODE != MODE_FWD) || !RIN || PAIR;    // complex values in the core
     constexpr bool COUT = (MODE == MODE_FWD) || !ROUT || PAIR;  // complex values out of the core
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
     float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
     const int tile = tile0 + blockIdx.x * kMixWarps + warp;
     if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
-    const int64_t base = (int64_t)blockIdx.y * a.n3;   // unpaired volume offset (values)
+    // unpaired volume offset (values): ragged batches pass a table of point offsets
+    const int64_t base = voff ? voff[blockIdx.y] : (int64_t)blockIdx.y * a.n3;
     const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;  // paired: first volume of the pair
     const int o0 = a.tile_off[tile];
     const int cnt = a.tile_off[tile + 1] - o0;

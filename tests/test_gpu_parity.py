@@ -231,3 +231,61 @@ def test_tensor_core_form_in_a_fresh_process():
     out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert float(out.stdout.strip().splitlines()[-1]) < 1e-6
+
+
+# --- ragged batches and CUDA-graph capture -------------------------------------
+
+def _ragged_volumes(orders, seed):
+    vols = [inputs.smoothed_noise(n, 1, seed=seed + i)[0] for i, n in enumerate(orders)]
+    return vols, np.concatenate([v.reshape(-1) for v in vols])
+
+
+@pytest.mark.parametrize("dtype", ["r32", "c32"])
+def test_ragged_orders_8_to_96_grouped_by_order(dtype):
+    orders = inputs.ragged_orders(30, seed=4)
+    vols, flat = _ragged_volumes(orders, seed=100)
+    if dtype == "c32":
+        flat = flat + 1j * np.roll(flat, 7)
+    with binding.Plan(orders=orders, dtype=dtype) as p:
+        y = p.forward(dev(flat, np.float32 if dtype == "r32" else np.complex64)).cpu().numpy()
+        assert p.launches(0) < 5 * len(set(orders))   # per-order launches, not per volume
+    off = 0
+    for i, n in enumerate(orders):
+        v = flat[off:off + n ** 3].reshape(n, n, n).astype(np.complex64 if dtype == "c32" else np.float32)
+        ref = oracle.forward_sum_fft(v.astype(np.complex128 if dtype == "c32" else np.float64), n).reshape(-1)
+        assert rel(y[off:off + n ** 3], ref) < TOL[dtype], (i, n)
+        off += n ** 3
+
+
+def test_ragged_odd_offsets_fall_back_correctly():
+    orders = [5, 8, 24, 3, 16]   # the even orders start at odd point offsets
+    vols, flat = _ragged_volumes(orders, seed=7)
+    with binding.Plan(orders=orders, dtype="r32") as p:
+        y = p.forward(dev(flat, np.float32)).cpu().numpy()
+    off = 0
+    for v, n in zip(vols, orders):
+        ref = oracle.forward_sum_fft(v.astype(np.float32).astype(np.float64), n).reshape(-1)
+        assert rel(y[off:off + n ** 3], ref) < TOL["r32"]
+        off += n ** 3
+
+
+@pytest.mark.parametrize("orders", [[64] * 4, [8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96]])
+def test_forward_captured_in_cuda_graph(orders):
+    vols, flat = _ragged_volumes(orders, seed=3)
+    with binding.Plan(orders=orders, dtype="r32") as p:
+        x = dev(flat, np.float32)
+        y = torch.empty(p.points, dtype=torch.complex64, device=DEV)
+        p.forward(x, out=y)            # warm-up outside the capture (sets kernel attributes)
+        ref = y.clone()
+        y.zero_()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.forward(x, out=y)
+        torch.cuda.current_stream().wait_stream(s)
+        y.zero_()
+        g.replay()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
