@@ -147,6 +147,120 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+FORM_NAMES = {"r32": "plain FP32 (SIMT orbit cores)",
+              "r32_bf16x3": "tensor-core (tcgen05 BF16, 3-term split inputs) orbit-core",
+              "r32_tf32x3": "tensor-core (tcgen05 TF32, 3-term split inputs) orbit-core"}
+
+
+def sampled_accuracy(x, y, n, dev, rows=24):
+    """Relative L2 error against the FP64 oracle, estimated from uniformly
+    sampled whole rows of D on the first volume (an unbiased estimate of the
+    whole-output relative L2), and the largest sampled error."""
+    import numpy as np
+    import torch
+    try:
+        import oracle
+        r = np.random.default_rng(3).integers(0, n ** 3, size=rows)
+        vol = x[:n ** 3].double().cpu().numpy()
+        ref = oracle.forward_rows(vol, n, r, nthreads=len(os.sched_getaffinity(0)))
+        got = y[torch.from_numpy(r).to(dev)].cpu().numpy()
+        rms = torch.sqrt(torch.mean(torch.abs(y[:n ** 3].to(torch.complex128)) ** 2)).item()
+        err = np.abs(got - ref)
+        return {"rel_l2_est": float(np.sqrt(np.mean(err ** 2)) / rms), "max_err_over_rms": float(err.max() / rms),
+                "rows": rows, "oracle": "FP64 direct definition"}
+    except Exception as exc:  # accuracy is reported, never required
+        return {"error": str(exc)}
+
+
+def _time(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def secondary_configs(dev):
+    """The other workloads, each short: order 64 x 256 round trip; a ragged
+    batch of 1000 volumes (orders 8..96) grouped by order in a CUDA graph vs
+    one launch set per volume; order 96 x 32 masked-reconstruction gradient
+    descent through the autograd wrapper."""
+    import numpy as np
+    import torch
+    from paper_1807_10058_gb300 import binding, inputs
+    from paper_1807_10058_gb300.autograd import fcc_dct
+    out = {}
+    # round trip, n = 64, batch 256 (smoothed noise)
+    n, b = 64, 256
+    x = torch.randn(b * n ** 3, device=dev)
+    with binding.Plan(n, b, "r32") as p:
+        y = torch.empty(b * n ** 3, dtype=torch.complex64, device=dev)
+        xr = torch.empty_like(x)
+        ms = _time(lambda: (p.forward(x, out=y), p.inverse(y, out=xr)), 5, 3)
+        rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
+    out["roundtrip_n64_b256"] = {"value": b * n ** 3 / (ms * 1e-3) / 1e9, "unit": "Gpoints/s (forward + inverse)",
+                                 "ms_per_step": ms, "roundtrip_rel_l2": rt, "data": "i.i.d. N(0,1) coefficients"}
+    # ragged, 1000 volumes
+    orders = inputs.ragged_orders(1000, seed=0)
+    tot = sum(o ** 3 for o in orders)
+    x = torch.randn(tot, device=dev)
+    y = torch.empty(tot, dtype=torch.complex64, device=dev)
+    with binding.Plan(orders=orders, dtype="r32") as p:
+        p.forward(x, out=y)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.forward(x, out=y)
+        torch.cuda.current_stream().wait_stream(s)
+        ms_graph = _time(g.replay, 5, 2)
+        ref = y.clone()
+        launches = p.launches(0)
+    os.environ["FCC_RAGGED_GROUPED"] = "0"
+    try:
+        with binding.Plan(orders=orders, dtype="r32") as q:
+            ms_per = _time(lambda: q.forward(x, out=y), 3, 1)
+            launches_per = q.launches(0)
+            same = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
+    finally:
+        del os.environ["FCC_RAGGED_GROUPED"]
+    out["ragged_1000"] = {"points": tot, "grouped_graph": {"value": tot / (ms_graph * 1e-3) / 1e9, "ms": ms_graph,
+                                                            "launches": launches},
+                          "per_volume": {"value": tot / (ms_per * 1e-3) / 1e9, "ms": ms_per, "launches": launches_per},
+                          "unit": "Gpoints/s", "rel_diff": same, "data": "i.i.d. N(0,1) coefficients, orders U{8..96}"}
+    # autograd: 50 gradient-descent steps of ||M . (D x) - b||^2, n = 96, batch 32
+    n, b = 96, 32
+    xt = inputs.phantom_device(n, b, seed=9, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4)
+    M = (torch.rand(b * n ** 3, generator=gen, device=dev) < 0.1).float()
+    with binding.Plan(n, b, "r32") as p:
+        bt = M * p.forward(xt)
+        x = torch.zeros(b * n ** 3, device=dev, requires_grad=True)
+
+        def step():
+            loss = torch.sum(torch.abs(M * fcc_dct(x, p) - bt) ** 2)
+            loss.backward()
+            with torch.no_grad():
+                x.sub_(1e-6 * x.grad)
+            x.grad = None
+            return loss
+        ms_gd = _time(step, 50, 3)
+        with torch.no_grad():
+            l0 = torch.sum(torch.abs(bt) ** 2).item()
+        final = step().item()
+    out["autograd_gd_n96_b32"] = {"ms_per_gd_step": ms_gd, "steps_timed": 50, "loss_ratio_after": final / l0,
+                                  "note": "forward + adjoint backward per step, step size 1e-6"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -155,8 +269,11 @@ def main():
     ap.add_argument("--impl", default="fcc", choices=["fcc", "reference"])
     ap.add_argument("--order", type=int, default=128)
     ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--dtype", default="r32")
+    ap.add_argument("--dtype", default="r32_bf16x3",
+                    help="form timed for the headline value (r32_bf16x3 = tensor-core form)")
+    ap.add_argument("--compare", default="r32", help="second form timed beside it ('' to skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -222,7 +339,7 @@ def main():
     # the split reads half a complex value and writes one complex output (8 B).
     paired = args.dtype.startswith("r") and batch >= 2
     if paired:
-        algo_bytes = {"mix_tiled_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12}
+        algo_bytes = {"mix_tiled_fwd": 8, "mix_tc_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12}
     else:
         algo_bytes = {"mix_tiled_fwd": 12, "fft_slab": 16, "fft_pencil": 16, "orbit_mix_fwd": 12,
                       "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16}
@@ -235,19 +352,7 @@ def main():
     step_gbs = 12 * pts / (ms * 1e-3) / 1e9
 
     # accuracy on sampled rows of one volume (outside the timed region)
-    accuracy = None
-    if rank == 0:
-        try:
-            import oracle
-            rows = np.random.default_rng(3).integers(0, n ** 3, size=8)
-            vol = x[:n ** 3].double().cpu().numpy()
-            ref = oracle.forward_rows(vol, n, rows, nthreads=len(os.sched_getaffinity(0)))
-            got = y[torch.from_numpy(rows).to(dev)].cpu().numpy()
-            scale = torch.sqrt(torch.mean(torch.abs(y[:n ** 3]) ** 2)).item()
-            accuracy = {"max_err_over_rms_sampled": float(np.abs(got - ref).max() / scale), "rows": 8,
-                        "oracle": "FP64 direct definition"}
-        except Exception as exc:  # accuracy is reported, never required
-            accuracy = {"error": str(exc)}
+    accuracy = sampled_accuracy(x, y, n, dev) if rank == 0 else None
 
     # end to end through the C ABI with host buffers
     xh = x.cpu().pin_memory()
@@ -265,6 +370,29 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3) / ke
 
+    # the comparison form on the same inputs (same timing rules)
+    compare = None
+    if args.compare and args.compare != args.dtype:
+        with binding.Plan(n, batch, args.compare) as q:
+            for _ in range(args.warmup):
+                q.forward(x, out=y)
+            torch.cuda.synchronize()
+            barrier()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(st)
+            for _ in range(args.steps):
+                q.forward(x, out=y)
+            c1.record(st)
+            torch.cuda.synchronize()
+            ms_c = c0.elapsed_time(c1) / args.steps
+            acc_c = sampled_accuracy(x, y, n, dev) if rank == 0 else None
+            compare = {"form": args.compare, "value": world * pts / (ms_c * 1e-3) / 1e9, "unit": UNIT,
+                       "ms_per_step": ms_c, "accuracy": acc_c}
+
+    extra = None
+    if rank == 0 and not args.no_extra and n == 128 and batch == 64:
+        extra = secondary_configs(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
@@ -273,10 +401,11 @@ def main():
         line = {
             "metric": METRIC, "value": world * pts / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"r32": "f32", "r32_bf16x3": "bf16x3/f32", "r32_tf32x3": "tf32x3/f32"}.get(args.dtype, args.dtype),
             "data": "synthetic CT-like phantoms (10-30 random ellipsoids, densities U[0,1], +N(0,1e-3^2)), seeded",
-            "config": {"workload": "FCC-DCT forward y = DCT_n x, order n=%d, batch %d, FP32 real -> complex64 "
-                                   "(plain FP32 form)" % (n, batch),
+            "config": {"workload": "FCC-DCT forward y = DCT_n x, order n=%d, batch %d, FP32 real -> complex64, "
+                                   "%s form" % (n, batch, FORM_NAMES.get(args.dtype, args.dtype)),
                        "order": n, "batch": batch, "points_per_step": pts, "form": args.dtype,
                        "l2": "inputs %.0f MB + outputs %.0f MB per step exceed the 126 MB L2"
                              % (pts * 4 / 1e6, pts * 8 / 1e6)},
@@ -291,6 +420,8 @@ def main():
             "gpu_launches": plan.launches(0) * args.steps,
             "clocks": ck,
             "accuracy": accuracy,
+            "compare": compare,
+            "secondary": extra,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -622,7 +622,7 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
         float* dst = out + v0 * a.n3 * 4;
         if (t.free_tiles > 0 && t.tc_a_image) {
             const int ngroups = (t.free_tiles + 3) / 4;
-            const int per_sm = bf16 ? 3 : 1;
+            const int per_sm = bf16 ? 4 : 2;   // blocks per SM allowed by shared memory and TMEM
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);

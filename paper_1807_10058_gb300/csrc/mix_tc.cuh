@@ -47,7 +47,12 @@ struct TcLayout {
     static constexpr size_t b_bytes = (size_t)TERMS * MAT;
     static constexpr size_t out_stride = 25;              // float2 per orbit row (24 + pad)
     static constexpr size_t out_bytes = 128 * out_stride * 8;
-    static constexpr size_t smem = a_bytes + b_bytes + out_bytes + 128 * (4 + 1 + 1) + 64;
+    // the epilogue reuses the consumed B operand: a per-warp transpose of 16
+    // orbits x (8 slots x 4 parts + pad), then the staged output rows
+    static constexpr size_t xch_floats = 16 * 36;
+    static constexpr size_t xch_bytes = 3 * xch_floats * 4;
+    static_assert(xch_bytes + out_bytes <= b_bytes, "epilogue staging must fit in the B operand");
+    static constexpr size_t smem = a_bytes + b_bytes + 128 * (4 + 1 + 1) + 64;
     static constexpr uint32_t idesc = (1u << 4) | ((KIND == 0 ? 1u : 2u) << 7) | ((KIND == 0 ? 1u : 2u) << 10) |
                                       ((128u >> 3) << 17) | ((128u >> 4) << 24);
     // byte offset of element (row r, k) inside one operand
@@ -104,15 +109,15 @@ __device__ __forceinline__ void store_terms(unsigned char* B, int n, int g, floa
 // grid.x: blocks looping over groups of 4 free tiles; grid.y: pairs of real volumes.
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads) mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out,
+__global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out,
                                                                      const TiledMixArgs a, int nfree_tiles,
                                                                      const uint4* __restrict__ a_image, int* status) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* As = smem_raw;
     unsigned char* Bs = As + L::a_bytes;
-    float2* outs = reinterpret_cast<float2*>(Bs + L::b_bytes);                  // [128][25]
-    uint32_t* s_rep = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(outs) + L::out_bytes);
+    float2* outs = reinterpret_cast<float2*>(Bs + L::xch_bytes);                // [128][25], inside B
+    uint32_t* s_rep = reinterpret_cast<uint32_t*>(Bs + L::b_bytes);
     uint8_t* s_pb = reinterpret_cast<uint8_t*>(s_rep + 128);
     uint8_t* s_pc = s_pb + 128;
     uint64_t* bar = reinterpret_cast<uint64_t*>(s_pc + 128 + 24);              // 8-byte aligned
@@ -225,27 +230,27 @@ __global__ void __launch_bounds__(kTcThreads) mix_tc_fwd_pair_kernel(const float
         // shared memory (aliasing the consumed B operand) -> lane = orbit combines
         // A1 + A2 / sqrt 2 for its 8 slots, applies R_g / 24, stages [orbit][slot].
         if (ok && warp < 3) {
-            float* xch = reinterpret_cast<float*>(Bs) + warp * (32 * 36);   // [32 orbits][8 slots x 4 parts + pad]
+            float* xch = reinterpret_cast<float*>(Bs) + warp * L::xch_floats;   // [16 orbits][36]
             const int s_own = lane >> 2, p_own = lane & 3;
+            const int half = lane >> 4, ol = lane & 15;    // two lanes per orbit: slots 4 half .. 4 half + 3
 #pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 32) {
-                uint32_t v[32];
+            for (int c0 = 0; c0 < 128; c0 += 16) {
+                uint32_t v[16];
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-                      "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-                      "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                      "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                      "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                for (int j = 0; j < 32; ++j) xch[j * 36 + s_own * 4 + p_own] = __uint_as_float(v[j]);
+                for (int j = 0; j < 16; ++j) xch[j * 36 + s_own * 4 + p_own] = __uint_as_float(v[j]);
                 __syncwarp();
-                const int col = c0 + lane;
+                const int col = c0 + ol;
                 const uint32_t rp = s_rep[col];
 #pragma unroll
-                for (int s8 = 0; s8 < 8; ++s8) {
-                    const float4 q4 = *reinterpret_cast<const float4*>(xch + lane * 36 + s8 * 4);
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const int s8 = 4 * half + s4;
+                    const float4 q4 = *reinterpret_cast<const float4*>(xch + ol * 36 + s8 * 4);
                     const float re = fmaf(q4.z, rs2, q4.x), im = fmaf(q4.w, rs2, q4.y);
                     const int g = 8 * warp + s8;
                     int q = rep_dot(rp, c_u[g][0], c_u[g][1], c_u[g][2]);
