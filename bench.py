@@ -37,6 +37,44 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def slowest_rank_ms(ms, dist, device):
+    """Replicas: every rank times its own batch; the job's time is the slowest
+    rank's (no data-path collective, only this reduction)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def rank_seed(rank):
+    """Seed of a rank's synthetic batch (ranks transform different volumes)."""
+    return 1000 * int(rank)
+
+
+def _traffic(kernel, points_per_launch):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/kernel_traffic.json), scaled to the launch size; None when the
+    kernel sources changed since the capture or the kernel was not captured."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "kernel_traffic.json")) as f:
+            d = json.load(f)
+        csrc = os.path.join(ROOT, "paper_1807_10058_gb300", "csrc")
+        h = hashlib.sha256()
+        for name in sorted(os.listdir(csrc)):
+            h.update(name.encode())
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != d["csrc_sha256"] or kernel not in d["kernels"]:
+            return None
+        k = d["kernels"][kernel]
+        return (k["dram_read"] + k["dram_write"]) * points_per_launch / d["points_per_launch"]
+    except Exception:
+        return None
+
+
 class Clocks:
     """nvidia-smi sampler for the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -295,7 +333,7 @@ def main():
     pts = batch * n ** 3
     dev = torch.device("cuda", local)
 
-    x = inputs.phantom_device(n, batch, seed=1000 * rank, device=dev)
+    x = inputs.phantom_device(n, batch, seed=rank_seed(rank), device=dev)
     plan = binding.Plan(n, batch, args.dtype)
     y = torch.empty(pts, dtype=torch.complex64, device=dev)
     st = torch.cuda.current_stream(dev)
@@ -321,10 +359,7 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     ck = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = slowest_rank_ms(ms, dist, dev)
 
     # per-kernel durations: the same K steps again with per-launch events
     plan.profile(True)
@@ -349,6 +384,7 @@ def main():
     per_launch_pts = pts * args.steps / top_cnt
     peak, peak_kind = _peaks()
     achieved = algo_bytes.get(top_name, 12) * per_launch_pts / (per_launch_ms * 1e-3) / 1e9
+    traffic = _traffic(top_name, per_launch_pts) if n == 128 else None
     step_gbs = 12 * pts / (ms * 1e-3) / 1e9
 
     # accuracy on sampled rows of one volume (outside the timed region)
@@ -410,7 +446,7 @@ def main():
                        "l2": "inputs %.0f MB + outputs %.0f MB per step exceed the 126 MB L2"
                              % (pts * 4 / 1e6, pts * 8 / 1e6)},
             "roofline": {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_point": algo_bytes.get(top_name, 12)},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": 12},
