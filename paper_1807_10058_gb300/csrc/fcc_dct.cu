@@ -59,7 +59,7 @@ struct OrderTables {
     uint8_t* tile_pc = nullptr;
     int free_tiles = 0;
     // tensor-core dtypes: the A operand image of the free-orbit forward core
-    void* tc_a_image = nullptr;
+    void* tc_core_image = nullptr;
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
@@ -180,10 +180,10 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     t.free_tiles = hp.free_tiles;
     if (is_tc(p->dtype) && hp.free_class >= 0) {
         std::vector<unsigned char> img;
-        const bool ok = p->dtype == FCC_R32_BF16X3 ? build_tc_a_image<0>(hp.classes[hp.free_class].fwd.data(), img)
-                                                   : build_tc_a_image<1>(hp.classes[hp.free_class].fwd.data(), img);
+        const bool ok = p->dtype == FCC_R32_BF16X3 ? build_tc_core_image<0>(hp.classes[hp.free_class].fwd.data(), img)
+                                                   : build_tc_core_image<1>(hp.classes[hp.free_class].fwd.data(), img);
         if (!ok) return FCC_ERR_UNSUPPORTED;
-        if ((s = upload(p, &t.tc_a_image, img.data(), img.size()))) return s;
+        if ((s = upload(p, &t.tc_core_image, img.data(), img.size()))) return s;
     }
     if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
@@ -620,20 +620,20 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
         const int64_t nv = std::min<int64_t>(65535, np - v0);
         const float* src = in + v0 * a.n3 * 2;
         float* dst = out + v0 * a.n3 * 4;
-        if (t.free_tiles > 0 && t.tc_a_image) {
+        if (t.free_tiles > 0 && t.tc_core_image) {
             const int ngroups = (t.free_tiles + 3) / 4;
-            const int per_sm = bf16 ? 4 : 2;   // blocks per SM allowed by shared memory and TMEM
+            const int per_sm = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);
             if (bf16)
                 mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
-                                                                          (const uint4*)t.tc_a_image, p->d_status);
+                                                                          (const uint4*)t.tc_core_image, p->d_status);
             else
                 mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
-                                                                          (const uint4*)t.tc_a_image, p->d_status);
+                                                                          (const uint4*)t.tc_core_image, p->d_status);
         }
-        if (!t.tc_a_image) {   // no free orbits at this order: every tile is a boundary tile
+        if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
             ProfScope ps("mix_tiled_fwd", st);
             mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, mix_tiled_smem_core(t.n), st>>>(
@@ -681,7 +681,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             const float* x = in + 2 * p0 * n3;
             float* y = out + 2 * p0 * n3 * 2;
             const int part = split_boundary ? 1 : 0;
-            if (is_tc(p->dtype) && t.tc_a_image) {
+            if (is_tc(p->dtype) && t.tc_core_image) {
                 s = launch_mix_tc_pairs(p, t, x, y, np, ss);
                 if (!s && !split_boundary && t.ntiles > t.free_tiles)
                     s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, 2);

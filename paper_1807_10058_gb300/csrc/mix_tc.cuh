@@ -5,17 +5,25 @@
 // unity.  In real form, with outputs (Re Z_g, Im Z_g) and inputs
 // (Re x_h, Im x_h), the 48 x 48 matrix has entries 0, +-1, +-1/sqrt(2); it is
 // split exactly as A1 + A2 / sqrt(2) with A1, A2 in {0, +-1}, both exact in
-// BF16 and TF32.  The FP32 inputs are split into three terms of the MMA
-// input type (x = x0 + x1 + x2; 24 / 33 significant bits for BF16 / TF32),
-// so D = A (x0 + x1 + x2) is accumulated in FP32 on the tensor cores with no
-// rounding of the operands.  The epilogue forms A1 x + A2 x / sqrt(2),
-// applies the row phase R_g / 24 and scatters as the SIMT kernel does.
+// BF16 and TF32.  The FP32 inputs are split into terms of the MMA input type
+// (BF16: x = x0 + x1 + x2, 24 significant bits; TF32: x = x0 + x1, the
+// second term rounded again, 22 bits), so the products with the exact core
+// lose nothing but the last bits of x and accumulate in FP32 on the tensor
+// cores.  With the core exact, the TF32 form's third product of a 2-way split
+// (low part of the matrix times high part of x) is identically zero.
 //
-// Block = 4 warps = 4 tiles of the plan (<= 128 orbits), one MMA tile
-// M = 128 (rows 32w + 4s + p: output slot g = 8w + s, part p = A1 re, A1 im,
-// A2 re, A2 im; rows 96..127 are zero), N = 128 (orbits), K = 48 per term.
-// Operands are K-major, no swizzle: 8-row x 16-byte core matrices, LBO =
-// 128 bytes between core matrices along K, SBO between 8-row groups.
+// MMA orientation: one row per orbit.  D (M = 128 orbits x N = 96) =
+// X (128 x K) * C^T, K = 48 real inputs per term (column 2h + c: slot h, real
+// or imaginary part), C (96 x K) the core image with row 4g + p: output slot
+// g, part p = A1 re, A1 im, A2 re, A2 im.  Both operands are K-major without
+// swizzle: 8-row x 16-byte core matrices, LBO = 128 bytes between core
+// matrices along K, SBO between 8-row groups.  Thread t owns orbit t of the
+// block's tile: it writes row t of X and reads TMEM lane t in the epilogue,
+// so no transpose is needed anywhere.
+//
+// Pipeline per block (4 warps = 4 tiles of the plan, <= 128 orbits): the
+// gather loads of the next tile are issued right after the MMAs of the
+// current one and are in flight during its completion wait and epilogue.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -39,22 +47,17 @@ struct TcLayout {
     static constexpr int ES = KIND == 0 ? 2 : 4;          // bytes per element
     static constexpr int KE = 16 / ES;                    // elements per core-matrix row
     static constexpr int KI = KIND == 0 ? 16 : 8;         // K per MMA instruction
+    static constexpr int TERMS = KIND == 0 ? 3 : 2;
+    static constexpr int NOUT = 96;                       // 24 slots x 4 parts
     static constexpr uint32_t LBO = 128;                  // K-direction core stride
     static constexpr uint32_t SBO = (kTcK / KE) * 128;    // 8-row group stride
-    static constexpr uint32_t MAT = 16 * SBO;             // one 128 x 48 operand
-    static constexpr int TERMS = 3;
-    static constexpr size_t a_bytes = MAT;
-    static constexpr size_t b_bytes = (size_t)TERMS * MAT;
-    static constexpr size_t out_stride = 25;              // float2 per orbit row (24 + pad)
-    static constexpr size_t out_bytes = 128 * out_stride * 8;
-    // the epilogue reuses the consumed B operand: a per-warp transpose of 16
-    // orbits x (8 slots x 4 parts + pad), then the staged output rows
-    static constexpr size_t xch_floats = 16 * 36;
-    static constexpr size_t xch_bytes = 3 * xch_floats * 4;
-    static_assert(xch_bytes + out_bytes <= b_bytes, "epilogue staging must fit in the B operand");
-    static constexpr size_t smem = a_bytes + b_bytes + 128 * (4 + 1 + 1) + 64;
+    static constexpr uint32_t XMAT = 16 * SBO;            // one 128 x 48 data term
+    static constexpr uint32_t CMAT = (NOUT / 8) * SBO;    // the 96 x 48 core
+    static constexpr size_t core_bytes = CMAT;
+    static constexpr size_t smem = CMAT + (size_t)TERMS * XMAT + 64;
     static constexpr uint32_t idesc = (1u << 4) | ((KIND == 0 ? 1u : 2u) << 7) | ((KIND == 0 ? 1u : 2u) << 10) |
-                                      ((128u >> 3) << 17) | ((128u >> 4) << 24);
+                                      ((uint32_t)(NOUT >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr int blocks_per_sm = KIND == 0 ? 4 : 3;   // shared memory; TMEM allows 4
     // byte offset of element (row r, k) inside one operand
     __host__ __device__ static constexpr uint32_t off(int r, int k) {
         return (uint32_t)((r / 8) * SBO + (k / KE) * LBO + (r % 8) * 16 + (k % KE) * ES);
@@ -77,31 +80,43 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(u);
 }
 
-// Store the three-term split of (re, im) at column n, rows k = 2g, 2g + 1.
+// Row `row` of the data operand: the split of the 48 inputs of one orbit,
+// 16 bytes (one core-matrix row) per store.
 template <int KIND>
-__device__ __forceinline__ void store_terms(unsigned char* B, int n, int g, float re, float im) {
+__device__ __forceinline__ void store_row(unsigned char* X, int row, const float* vr, const float* vi) {
     using L = TcLayout<KIND>;
-    const uint32_t o = L::off(n, 2 * g);
     if (KIND == 0) {
-        float rr = re, ri = im;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const __nv_bfloat16 hr = __float2bfloat16_rn(rr), hi = __float2bfloat16_rn(ri);
-            __nv_bfloat162 v;
-            v.x = hr;
-            v.y = hi;
-            *reinterpret_cast<__nv_bfloat162*>(B + t * L::MAT + o) = v;
-            rr -= __bfloat162float(hr);
-            ri -= __bfloat162float(hi);
+        for (int c = 0; c < kTcK / 8; ++c) {   // slots 4c .. 4c + 3
+            float r[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                r[2 * e] = vr[4 * c + e];
+                r[2 * e + 1] = vi[4 * c + e];
+            }
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
+                    w[e] = *reinterpret_cast<const uint32_t*>(&h);
+                    if (t < 2) {
+                        r[2 * e] -= __low2float(h);
+                        r[2 * e + 1] -= __high2float(h);
+                    }
+                }
+                *reinterpret_cast<uint4*>(X + t * L::XMAT + L::off(row, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
         }
     } else {
-        float rr = re, ri = im;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const float tr = tf32_round(rr), ti = tf32_round(ri);
-            *reinterpret_cast<float2*>(B + t * L::MAT + o) = make_float2(tr, ti);
-            rr -= tr;
-            ri -= ti;
+        for (int c = 0; c < kTcK / 4; ++c) {   // slots 2c, 2c + 1
+            const float r0 = vr[2 * c], i0 = vi[2 * c], r1 = vr[2 * c + 1], i1 = vi[2 * c + 1];
+            const float hr0 = tf32_round(r0), hi0 = tf32_round(i0), hr1 = tf32_round(r1), hi1 = tf32_round(i1);
+            *reinterpret_cast<float4*>(X + L::off(row, 4 * c)) = make_float4(hr0, hi0, hr1, hi1);
+            *reinterpret_cast<float4*>(X + L::XMAT + L::off(row, 4 * c)) =
+                make_float4(tf32_round(r0 - hr0), tf32_round(i0 - hi0), tf32_round(r1 - hr1), tf32_round(i1 - hi1));
         }
     }
 }
@@ -109,18 +124,14 @@ __device__ __forceinline__ void store_terms(unsigned char* B, int n, int g, floa
 // grid.x: blocks looping over groups of 4 free tiles; grid.y: pairs of real volumes.
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                                     const TiledMixArgs a, int nfree_tiles,
-                                                                     const uint4* __restrict__ a_image, int* status) {
+__global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
+mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
+                       const uint4* __restrict__ core_image, int* status) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* As = smem_raw;
-    unsigned char* Bs = As + L::a_bytes;
-    float2* outs = reinterpret_cast<float2*>(Bs + L::xch_bytes);                // [128][25], inside B
-    uint32_t* s_rep = reinterpret_cast<uint32_t*>(Bs + L::b_bytes);
-    uint8_t* s_pb = reinterpret_cast<uint8_t*>(s_rep + 128);
-    uint8_t* s_pc = s_pb + 128;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(s_pc + 128 + 24);              // 8-byte aligned
+    unsigned char* Cs = smem_raw;                 // core, 96 x 48
+    unsigned char* Xs = Cs + L::CMAT;             // data terms, 128 x 48 each
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Xs + L::TERMS * L::XMAT);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -128,9 +139,8 @@ __global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair
     const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;
     const float2* __restrict__ ph = a.phase;
 
-    // the A operand: one image, loaded once per block
-    for (int e = tid; e < (int)(L::a_bytes / 16); e += kTcThreads)
-        reinterpret_cast<uint4*>(As)[e] = a_image[e];
+    for (int e = tid; e < (int)(L::core_bytes / 16); e += kTcThreads)
+        reinterpret_cast<uint4*>(Cs)[e] = core_image[e];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)), "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -143,64 +153,54 @@ __global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *s_tmem;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
 
     const float rs2 = 0.70710678118654752440f;
+    const float sc = 1.0f / 24.0f;
     const int ngroups = (nfree_tiles + 3) / 4;
     uint32_t phase = 0;
     bool ok = true;
 
-    for (int grp = blockIdx.x; grp < ngroups && ok; grp += gridDim.x) {
-        // ---- gather this warp's tile into the B operand (three terms)
+    // gather of one tile into registers: thread = orbit, all 48 loads in flight
+    float vr[24], vi[24];
+    uint32_t nrep = 0;
+    bool nact = false;
+    auto gather = [&](int grp) {
         const int tile = grp * 4 + warp;
-        const bool have = tile < nfree_tiles;
         int o0 = 0, cnt = 0;
-        if (have) {
-            o0 = a.tile_off[tile];
-            cnt = a.tile_off[tile + 1] - o0;
+        if (tile < nfree_tiles) {
+            o0 = __ldg(a.tile_off + tile);
+            cnt = __ldg(a.tile_off + tile + 1) - o0;
         }
-        const bool act = lane < cnt;
-        uint32_t myrep = 0;
-        int rsel[4] = {lane, lane, lane, lane};
-        if (act) {
-            myrep = __ldg(a.reps + o0 + lane);
-            rsel[1] = __ldg(a.permb + o0 + lane);
-            rsel[2] = __ldg(a.permc + o0 + lane);
-        }
-        s_rep[warp * 32 + lane] = myrep;
-        {
-            float vr[24], vi[24];
-            static_for<0, 24>([&](auto Gc) {
-                constexpr int g = decltype(Gc)::value;
-                const int r = rsel[WD<g>::v];
-                const int gi = __shfl_sync(0xffffffffu, rep_dot(myrep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3], r);
-                vr[g] = 0.f;
-                vi[g] = 0.f;
-                if (act) {
-                    vr[g] = __ldg(in + pb + gi);
-                    vi[g] = __ldg(in + pb + a.n3 + gi);
-                }
-            });
-            if (act) {
-                static_for<0, 24>([&](auto Gc) {
-                    constexpr int g = decltype(Gc)::value;
-                    store_terms<KIND>(Bs, warp * 32 + rsel[WD<g>::v], g, vr[g], vi[g]);
-                });
-            }
-        }
+        nact = lane < cnt;
+        nrep = nact ? __ldg(a.reps + o0 + lane) : 0u;
+        static_for<0, 24>([&](auto Gc) {
+            constexpr int g = decltype(Gc)::value;
+            const int gi = rep_dot(nrep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
+            vr[g] = nact ? __ldg(in + pb + gi) : 0.f;
+            vi[g] = nact ? __ldg(in + pb + a.n3 + gi) : 0.f;
+        });
+    };
+
+    int grp = blockIdx.x;
+    if (grp < ngroups) gather(grp);
+    for (; grp < ngroups && ok; grp += gridDim.x) {
+        const uint32_t rep = nrep;
+        const bool act = nact;
+        store_row<KIND>(Xs, tid, vr, vi);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- one thread issues the MMAs and commits to the barrier
         if (tid == 0) {
-            const uint32_t ab = smem_addr(As), bb = smem_addr(Bs);
+            const uint32_t xb = smem_addr(Xs), cb = smem_addr(Cs);
 #pragma unroll
             for (int t = 0; t < L::TERMS; ++t) {
 #pragma unroll
                 for (int ks = 0; ks < kTcK / L::KI; ++ks) {
                     const uint32_t koff = (uint32_t)(ks * L::KI / L::KE) * L::LBO;
-                    const uint64_t da = umma_desc(ab + koff, L::LBO, L::SBO);
-                    const uint64_t db = umma_desc(bb + t * L::MAT + koff, L::LBO, L::SBO);
+                    const uint64_t da = umma_desc(xb + t * L::XMAT + koff, L::LBO, L::SBO);
+                    const uint64_t db = umma_desc(cb + koff, L::LBO, L::SBO);
                     const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
                     if (KIND == 0)
                         asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
@@ -212,6 +212,9 @@ __global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
         }
+        // the next tile's loads overlap the MMAs, the wait and this epilogue
+        const int nxt = grp + (int)gridDim.x;
+        if (nxt < ngroups) gather(nxt);
         uint32_t done = 0;
         for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
             asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -225,67 +228,50 @@ __global__ void __launch_bounds__(kTcThreads, KIND == 0 ? 4 : 2) mix_tc_fwd_pair
             ok = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---- epilogue: warp w < 3 holds rows 32w + 4s + p (slot g = 8w + s, part
-        // p).  Per chunk of 32 orbits: TMEM -> registers -> a per-warp transpose in
-        // shared memory (aliasing the consumed B operand) -> lane = orbit combines
-        // A1 + A2 / sqrt 2 for its 8 slots, applies R_g / 24, stages [orbit][slot].
-        if (ok && warp < 3) {
-            float* xch = reinterpret_cast<float*>(Bs) + warp * L::xch_floats;   // [16 orbits][36]
-            const int s_own = lane >> 2, p_own = lane & 3;
-            const int half = lane >> 4, ol = lane & 15;    // two lanes per orbit: slots 4 half .. 4 half + 3
-#pragma unroll 1
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-                uint32_t v[16];
+        if (ok) {
+            // epilogue: TMEM lane = this thread's orbit; 32 columns = 8 slots per load
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint32_t v[32];
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-                      "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                      "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                      "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(trow + (uint32_t)(32 * c)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int j = 0; j < 16; ++j) xch[j * 36 + s_own * 4 + p_own] = __uint_as_float(v[j]);
-                __syncwarp();
-                const int col = c0 + ol;
-                const uint32_t rp = s_rep[col];
-#pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    const int s8 = 4 * half + s4;
-                    const float4 q4 = *reinterpret_cast<const float4*>(xch + ol * 36 + s8 * 4);
-                    const float re = fmaf(q4.z, rs2, q4.x), im = fmaf(q4.w, rs2, q4.y);
-                    const int g = 8 * warp + s8;
-                    int q = rep_dot(rp, c_u[g][0], c_u[g][1], c_u[g][2]);
+                static_for<0, 8>([&](auto Sc) {
+                    constexpr int s8 = decltype(Sc)::value;
+                    const int g = 8 * c + s8;
+                    const float re = fmaf(__uint_as_float(v[4 * s8 + 2]), rs2, __uint_as_float(v[4 * s8]));
+                    const float im = fmaf(__uint_as_float(v[4 * s8 + 3]), rs2, __uint_as_float(v[4 * s8 + 1]));
+                    int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
                     q = q < 0 ? q + M8 : q;
-                    const float2 R = __ldg(ph + q);
-                    const float sc = 1.0f / 24.0f;
-                    outs[col * L::out_stride + g] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
-                }
-                __syncwarp();
+                    const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
+                    if (act) {
+                        const float2 R = __ldg(ph + q);
+                        reinterpret_cast<float2*>(out)[pb + gi] =
+                            make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
+                    }
+                });
             }
         }
+        // TMEM reads complete before the next tile's MMAs (issued after the next barrier)
         asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        // ---- scatter this warp's tile (all slots of a free orbit are canonical)
-        if (ok) {
-            static_for<0, 24>([&](auto Gc) {
-                constexpr int g = decltype(Gc)::value;
-                const int r = rsel[WD<g>::v];
-                const int gi = __shfl_sync(0xffffffffu, rep_dot(myrep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3], r);
-                if (act) reinterpret_cast<float2*>(out)[pb + gi] = outs[(warp * 32 + r) * L::out_stride + g];
-            });
-        }
-        __syncthreads();   // the next gather overwrites B and the staging rows
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
-// Host side: the A image (rows 32w + 4s + p, columns 2h + c) in the operand
+// Host side: the core image (row 4g + p, column 2h + c) in the operand
 // layout, from the free-orbit forward core fwd (24 x 24 complex, = E / 24).
 template <int KIND>
-inline bool build_tc_a_image(const std::complex<double>* fwd, std::vector<unsigned char>& img) {
+inline bool build_tc_core_image(const std::complex<double>* fwd, std::vector<unsigned char>& img) {
     using L = TcLayout<KIND>;
-    img.assign(L::a_bytes, 0);
+    img.assign(L::core_bytes, 0);
     const double h = std::sqrt(0.5);
     auto put = [&](int r, int k, double v) {
         const uint32_t o = L::off(r, k);
@@ -298,7 +284,6 @@ inline bool build_tc_a_image(const std::complex<double>* fwd, std::vector<unsign
         }
     };
     for (int g = 0; g < 24; ++g) {
-        const int w = g / 8, s = g % 8;
         for (int hh = 0; hh < 24; ++hh) {
             const std::complex<double> c = fwd[g * 24 + hh] * 24.0;   // an 8th root of unity
             const double cr = c.real(), ci = c.imag();
@@ -308,7 +293,7 @@ inline bool build_tc_a_image(const std::complex<double>* fwd, std::vector<unsign
             if (!odd && !even) return false;
             const double sr = odd ? cr / h : cr, si = odd ? ci / h : ci;   // +-1 or 0
             const int pre = odd ? 2 : 0;   // A2 rows carry the 1/sqrt(2) entries
-            const int rre = 32 * w + 4 * s + pre, rim = rre + 1;
+            const int rre = 4 * g + pre, rim = rre + 1;
             put(rre, 2 * hh, sr);
             put(rre, 2 * hh + 1, -si);
             put(rim, 2 * hh, si);
