@@ -582,6 +582,24 @@ fcc_status launch_pair(bool split, int n, const float* in, float* out, int64_t n
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
+// Forward 3-D DFT of `np` paired chunks (Y of pair p at volume 2p of y) and
+// the split into D x1, D x2: the fast path fuses the split into the last
+// (pencil) pass; otherwise DFT passes then the split kernel.
+fcc_status dft3_split_pairs(const OrderTables& t, float* y, int64_t np, cudaStream_t st) {
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    if (has_fast_fft(t.n) && ((uintptr_t)y & 15u) == 0) {
+        const float2* tw = (const float2*)t.tw;
+        fcc_status s = fast_fft(t.n, true, +1, (const float2*)y, (float2*)y, np, tw, 2 * n3, st);
+        if (s) return s;
+        ProfScope ps("fft_pencil_pair", st);
+        return launch_fast_pencil_pair(t.n, (const float2*)y, (float2*)y, np, tw, 2 * n3, st) == cudaSuccess
+                   ? FCC_OK
+                   : FCC_ERR_CUDA;
+    }
+    fcc_status s = launch_dft3(t, +1, y, y, np, st, 2 * n3);
+    return s ? s : launch_pair(true, t.n, nullptr, y, np, st);
+}
+
 // Forward mixing of `np` pairs of real volumes with the orbit core on the
 // tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
@@ -690,8 +708,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             } else {
                 s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, part);
             }
-            if (!s) s = launch_dft3(t, +1, y, y, np, ss, 2 * n3);
-            if (!s) s = launch_pair(true, t.n, nullptr, y, np, ss);
+            if (!s) s = dft3_split_pairs(t, y, np, ss);
         } else {
             float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
             const float* y = in + 2 * p0 * n3 * 2;

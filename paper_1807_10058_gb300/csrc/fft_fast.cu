@@ -35,7 +35,36 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
     return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const float2* tw, int64_t vstride,
+                          cudaStream_t st) {
+    using L = FastLayout<N>;
+    if (vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        attr = true;
+    }
+    constexpr int CPB1 = kFastWarps * L::PPW;
+    const int64_t g = npairs * (N / 2 + 1) * ((N + CPB1 - 1) / CPB1);
+    if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+    fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
+                                    int64_t vstride, cudaStream_t st) {
+    switch (n) {
+#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st);
+        FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
+        FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
+#undef FCC_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
 
 bool has_fast_fft(int n) {
     switch (n) {

@@ -257,9 +257,113 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg,
     }
 }
 
+// Last pass of the forward transform of paired real volumes, fused with the
+// split of Y = D (x1 + i x2) into D x1 and D x2.  The pairing map
+// pi(i, l, q) = (i - l, -l, q - l) sends the pencil (l, q) along the slow
+// axis onto the pencil (n - l, q - l) with its index shifted by -l, so one
+// thread transforms both pencils, stages the partner's outputs in its
+// exchange slot and forms, for every output index k of its own pencil,
+//   y1 = (Y[k] + conj(P[k - l])) / 2,   y2 = (Y[k] - conj(P[k - l])) / (2i),
+// written at (k, l, q) of volumes 2p and 2p + 1, and their conjugates at
+// (k - l, n - l, q - l).  Primary rows l = 0 .. n/2: row 0 is its own partner,
+// in row n/2 only columns q < n/2 are primary, so every pencil is read and
+// written by exactly one thread.  grid.x = pairs * (n/2 + 1) * ceil(n / CPB1);
+// Y of pair p sits at p * vstride (vstride >= 2 n^3), y2 at p * vstride + n^3.
+template <int N>
+__global__ void __launch_bounds__(kFastThreads)
+fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
+    using L = FastLayout<N>;
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
+    constexpr int CPB1 = kFastWarps * PPW;
+    constexpr int CBLK = (N + CPB1 - 1) / CPB1;
+    constexpr int ROWS = N / 2 + 1;
+    constexpr int64_t NN = (int64_t)N * N, N3 = NN * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* exall = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = exall + kFastWarps * L::EXW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    __syncthreads();
+    const int64_t blk = blockIdx.x;
+    const int64_t pr = blk / (ROWS * CBLK);
+    const int rem = (int)(blk - pr * ROWS * CBLK);
+    const int l = rem / CBLK, cb = rem % CBLK;
+    const int qlim = 2 * l == N ? N / 2 : N;
+    const int cw = cb * CPB1 + warp * PPW;
+    if (cw >= qlim) return;   // warp-uniform; no block barrier below
+    const int cl = lane % PPW, j = lane / PPW;
+    const int c = cw + cl;
+    const bool act = c < qlim;
+    const int lp = (N - l) % N;
+    const int cp = (c - l + N) % N;
+    float2* ex = exall + warp * L::EXW + cl * L::EXP;
+    const int64_t vb = pr * vstride;
+    const int64_t ba = vb + (int64_t)l * N + c;     // own pencil; + k * NN
+    const int64_t bp = vb + (int64_t)lp * N + cp;   // partner pencil
+    float ar[R1], ai[R1], br[R1], bi[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+        const int64_t o = (int64_t)(j + G * m) * NN;
+        const float2 t = act ? in[ba + o] : make_float2(0.f, 0.f);
+        const float2 u = act ? in[bp + o] : make_float2(0.f, 0.f);
+        ar[m] = t.x;
+        ai[m] = t.y;
+        br[m] = u.x;
+        bi[m] = u.y;
+    }
+    float ur[2][E][G], ui[2][E][G];
+#pragma unroll
+    for (int pz = 0; pz < 2; ++pz) {
+        float* vr = pz ? br : ar;
+        float* vi = pz ? bi : ai;
+        pencil_stage1<N, 1>(vr, vi, j, ex, tw);
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+#pragma unroll
+            for (int jj = 0; jj < G; ++jj) {
+                const float2 t = ex[jj * (R1 + 1) + j + G * e];
+                ur[pz][e][jj] = t.x;
+                ui[pz][e][jj] = t.y;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        reg::Dft<G, 1, float>::run(ur[0][e], ui[0][e]);
+        reg::Dft<G, 1, float>::run(ur[1][e], ui[1][e]);
+#pragma unroll
+        for (int k1 = 0; k1 < G; ++k1) ex[j + G * e + R1 * k1] = make_float2(ur[1][e][k1], ui[1][e][k1]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+#pragma unroll
+        for (int k1 = 0; k1 < G; ++k1) {
+            const int k = j + G * e + R1 * k1;
+            int kp = k - l;
+            kp += kp < 0 ? N : 0;
+            const float2 B = ex[kp];
+            const float Ar = ur[0][e][k1], Ai = ui[0][e][k1];
+            const float2 y1 = make_float2(0.5f * (Ar + B.x), 0.5f * (Ai - B.y));
+            const float dr = 0.5f * (Ar - B.x), di = 0.5f * (Ai + B.y);   // y2 = -i d
+            if (act) {
+                out[ba + k * NN] = y1;
+                out[ba + N3 + k * NN] = make_float2(di, -dr);
+                out[bp + kp * NN] = make_float2(y1.x, -y1.y);
+                out[bp + N3 + kp * NN] = make_float2(di, dr);
+            }
+        }
+    }
+}
+
 // Host launchers (fft_fast.cu).
 bool has_fast_fft(int n);
 cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
                             const float2* tw, int64_t vstride, const int64_t* voff, cudaStream_t st);
+// forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
+cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
+                                    int64_t vstride, cudaStream_t st);
 
 }  // namespace fcc
