@@ -371,10 +371,12 @@ def main():
     # algorithmic bytes per real point of each kernel.  Real plans pair two
     # volumes per complex transform: the mixing reads x (4 B) and writes half a
     # complex value (4 B); each DFT pass reads and writes half a complex value;
-    # the split reads half a complex value and writes one complex output (8 B).
+    # the split (alone, or fused into the last DFT pass) reads half a complex
+    # value and writes one complex output (8 B).
     paired = args.dtype.startswith("r") and batch >= 2
     if paired:
-        algo_bytes = {"mix_tiled_fwd": 8, "mix_tc_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12}
+        algo_bytes = {"mix_tiled_fwd": 8, "mix_tc_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12,
+                      "fft_pencil_pair": 12}
     else:
         algo_bytes = {"mix_tiled_fwd": 12, "fft_slab": 16, "fft_pencil": 16, "orbit_mix_fwd": 12,
                       "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16}

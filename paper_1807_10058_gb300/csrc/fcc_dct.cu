@@ -94,6 +94,8 @@ struct fcc_plan {
     cudaStream_t streams[kMaxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t bnd_ev = nullptr;    // boundary tiles done (forward)
+    cudaStream_t bnd_stream = nullptr;   // boundary tiles, concurrent with the chunks' free mixing
+    cudaEvent_t bnd_join = nullptr;
     cudaEvent_t join_ev[kMaxStreams] = {};
     // per-kernel timing (fcc_dct_profile_enable)
     bool profiling = false;
@@ -238,6 +240,8 @@ void release(fcc_plan* p) {
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->bnd_ev) cudaEventDestroy(p->bnd_ev);
+    if (p->bnd_join) cudaEventDestroy(p->bnd_join);
+    if (p->bnd_stream) cudaStreamDestroy(p->bnd_stream);
     for (auto e : p->event_pool) cudaEventDestroy(e);
     cudaSetDevice(cur);
     delete p;
@@ -306,6 +310,8 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         }
         if (s == FCC_OK && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
         if (s == FCC_OK && cudaEventCreateWithFlags(&p->bnd_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
+        if (s == FCC_OK && cudaEventCreateWithFlags(&p->bnd_join, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
+        if (s == FCC_OK && cudaStreamCreateWithFlags(&p->bnd_stream, cudaStreamNonBlocking) != cudaSuccess) s = FCC_ERR_CUDA;
     }
     if (s == FCC_OK) {
         // workspace for inverse / adjoint: one chunk per internal stream
@@ -683,14 +689,14 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     const bool pairing = rin && p->pairing && nvol >= 2;
     const int64_t npairs = pairing ? nvol / 2 : 0;
     const int64_t cp = cv;   // pairs per chunk: one complex volume of intermediate per pair
-    // forward: the boundary (non-free) tiles of every pair in one launch on the
-    // first stream, before the chunks' DFT passes (each chunk waits for it)
+    // forward: the boundary (non-free) tiles of every pair in one launch on a
+    // stream of their own, concurrent with the chunks' free mixing; each
+    // chunk's DFT passes wait for it
     const bool split_boundary = which == 0 && npairs > 0 && t.free_tiles > 0 && t.ntiles > t.free_tiles;
     if (split_boundary) {
-        s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, npairs, 1.f, p->streams[0], true, 2);
-        if (!s && cudaEventRecord(p->bnd_ev, p->streams[0]) != cudaSuccess) s = FCC_ERR_CUDA;
-        for (int i = 1; i < ns && !s; ++i)
-            if (cudaStreamWaitEvent(p->streams[i], p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(p->bnd_stream, p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+        s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, npairs, 1.f, p->bnd_stream, true, 2);
+        if (!s && cudaEventRecord(p->bnd_ev, p->bnd_stream) != cudaSuccess) s = FCC_ERR_CUDA;
     }
     for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
         const int64_t np = std::min(cp, npairs - p0);
@@ -708,6 +714,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             } else {
                 s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, part);
             }
+            if (!s && split_boundary && cudaStreamWaitEvent(ss, p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
             if (!s) s = dft3_split_pairs(t, y, np, ss);
         } else {
             float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
@@ -739,6 +746,10 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     for (int i = 0; i < ns; ++i) {
         if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
         if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    if (split_boundary) {
+        if (cudaEventRecord(p->bnd_join, p->bnd_stream) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->bnd_join, 0) != cudaSuccess) return FCC_ERR_CUDA;
     }
     return s;
 }
