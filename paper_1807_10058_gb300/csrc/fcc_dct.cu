@@ -58,8 +58,10 @@ struct OrderTables {
     uint8_t* tile_pb = nullptr;
     uint8_t* tile_pc = nullptr;
     int free_tiles = 0;
-    // tensor-core dtypes: the A operand image of the free-orbit forward core
+    // tensor-core dtypes: the operand image of the free-orbit forward core and
+    // the free tiles' representatives padded to 32 per tile (0xffffffff = none)
     void* tc_core_image = nullptr;
+    uint32_t* tc_reps32 = nullptr;
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
@@ -186,6 +188,10 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
                                                    : build_tc_core_image<1>(hp.classes[hp.free_class].fwd.data(), img);
         if (!ok) return FCC_ERR_UNSUPPORTED;
         if ((s = upload(p, &t.tc_core_image, img.data(), img.size()))) return s;
+        std::vector<uint32_t> r32((size_t)std::max(1, hp.free_tiles) * 32, 0xffffffffu);
+        for (int tl = 0; tl < hp.free_tiles; ++tl)
+            for (int o = hp.tile_off[tl]; o < hp.tile_off[tl + 1]; ++o) r32[(size_t)tl * 32 + (o - hp.tile_off[tl])] = hp.tile_reps[o];
+        if ((s = upload(p, (void**)&t.tc_reps32, r32.data(), r32.size() * 4))) return s;
     }
     if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
@@ -651,10 +657,10 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);
             if (bf16)
-                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
+                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
                                                                           (const uint4*)t.tc_core_image, p->d_status);
             else
-                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles,
+                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
                                                                           (const uint4*)t.tc_core_image, p->d_status);
         }
         if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile

@@ -45,8 +45,7 @@ cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const f
         cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
         attr = true;
     }
-    constexpr int CPB1 = kFastWarps * L::PPW;
-    const int64_t g = npairs * (N / 2 + 1) * ((N + CPB1 - 1) / CPB1);
+    const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
     fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
     return cudaGetLastError();

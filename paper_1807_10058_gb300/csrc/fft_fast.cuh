@@ -50,7 +50,8 @@ struct FastLayout {
     static constexpr int LD = N + 4;                   // slab row stride (complex)
     static constexpr int EXP = G * (R1 + 1);           // exchange stride per pencil
     static constexpr int EXW = PPW * EXP;              // exchange per warp
-    // slab kernel: 16 warps when the slab and 16 exchange buffers fit in ~200 KB
+    // slab kernel: 16 warps when the slab and 16 exchange buffers fit in
+    // ~200 KB (leaving room on the SM for a block of another kernel)
     static constexpr int SW = ((size_t)(N * LD + 16 * EXW + N) * 8 <= 200 * 1024) ? 16 : 8;
     static constexpr int SLAB_THREADS = 32 * SW;
     static constexpr size_t slab_smem = (size_t)(N * LD + SW * EXW + N) * sizeof(float2);
@@ -134,22 +135,51 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, i
     {
         const int p = lane / G, j = lane % G;
         float2* ex = exall + warp * L::EXW + p * L::EXP;
-        for (int r0 = 0; r0 < N; r0 += SW * PPW) {
-            if (r0 + warp * PPW >= N) continue;   // warp-uniform
-            const int r = r0 + warp * PPW + p;
-            const bool act = r < N;
-            float vr[R1], vi[R1];
-            const float2* src = in + base + (int64_t)r * N + j;
+        constexpr int RR = SW * PPW;                    // rows per round
+        constexpr int NR = (N + RR - 1) / RR;           // rounds
+        if (NR > 1 && NR * R1 * 2 <= (SW == 8 ? 128 : 64)) {
+            // every round's loads in flight before the first transform
+            float vr[NR][R1], vi[NR][R1];
 #pragma unroll
-            for (int m = 0; m < R1; ++m) {
-                const float2 t = act ? src[G * m] : make_float2(0.f, 0.f);
-                vr[m] = t.x;
-                vi[m] = t.y;
+            for (int rd = 0; rd < NR; ++rd) {
+                const int r = rd * RR + warp * PPW + p;
+                const bool act = r < N;
+                const float2* src = in + base + (int64_t)r * N + j;
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = act ? src[G * m] : make_float2(0.f, 0.f);
+                    vr[rd][m] = t.x;
+                    vi[rd][m] = t.y;
+                }
             }
-            float2* row = slab + r * LD;
-            PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int c, float xr, float xi) {
-                if (act) row[c] = make_float2(xr, xi);
-            });
+#pragma unroll
+            for (int rd = 0; rd < NR; ++rd) {
+                if (rd * RR + warp * PPW >= N) continue;   // warp-uniform
+                const int r = rd * RR + warp * PPW + p;
+                const bool act = r < N;
+                float2* row = slab + r * LD;
+                PencilFft<N, S>::run(vr[rd], vi[rd], j, ex, tw, [&](int c, float xr, float xi) {
+                    if (act) row[c] = make_float2(xr, xi);
+                });
+            }
+        } else {
+            for (int r0 = 0; r0 < N; r0 += RR) {
+                if (r0 + warp * PPW >= N) continue;   // warp-uniform
+                const int r = r0 + warp * PPW + p;
+                const bool act = r < N;
+                float vr[R1], vi[R1];
+                const float2* src = in + base + (int64_t)r * N + j;
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = act ? src[G * m] : make_float2(0.f, 0.f);
+                    vr[m] = t.x;
+                    vi[m] = t.y;
+                }
+                float2* row = slab + r * LD;
+                PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int c, float xr, float xi) {
+                    if (act) row[c] = make_float2(xr, xi);
+                });
+            }
         }
     }
     __syncthreads();
@@ -260,22 +290,30 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg,
 // Last pass of the forward transform of paired real volumes, fused with the
 // split of Y = D (x1 + i x2) into D x1 and D x2.  The pairing map
 // pi(i, l, q) = (i - l, -l, q - l) sends the pencil (l, q) along the slow
-// axis onto the pencil (n - l, q - l) with its index shifted by -l, so one
-// thread transforms both pencils, stages the partner's outputs in its
-// exchange slot and forms, for every output index k of its own pencil,
-//   y1 = (Y[k] + conj(P[k - l])) / 2,   y2 = (Y[k] - conj(P[k - l])) / (2i),
-// written at (k, l, q) of volumes 2p and 2p + 1, and their conjugates at
-// (k - l, n - l, q - l).  Primary rows l = 0 .. n/2: row 0 is its own partner,
-// in row n/2 only columns q < n/2 are primary, so every pencil is read and
-// written by exactly one thread.  grid.x = pairs * (n/2 + 1) * ceil(n / CPB1);
-// Y of pair p sits at p * vstride (vstride >= 2 n^3), y2 at p * vstride + n^3.
+// axis onto the pencil (n - l, q - l) with its index shifted by -l.  Warps
+// 0-3 of a block transform primary pencils (l, q), warps 4-7 their partners;
+// both stage their outputs in shared memory, and every thread forms, for
+// each output index k of its own pencil with counterpart index k' (k - l on
+// a primary pencil, k + l on a partner),
+//   y1 = (Y[k] + conj(Y'[k'])) / 2,   y2 = (Y[k] - conj(Y'[k'])) / (2i),
+// written into volumes 2p and 2p + 1 at its own pencil.  Primary rows
+// l = 0 .. n/2: row 0 is its own partner (warps 4-7 idle), in row n/2 only
+// columns q < n/2 are primary, so every pencil is written exactly once.
+// grid.x = pairs * (n/2 + 1) * ceil(n / CPB2); Y of pair p sits at
+// p * vstride (vstride >= 2 n^3), y2 at p * vstride + n^3.
+template <int N>
+struct PairLayout {
+    static constexpr int PPW = FastLayout<N>::PPW;
+    static constexpr int CPB2 = (kFastWarps / 2) * PPW;   // primary columns per block
+    static constexpr int CBLK = (N + CPB2 - 1) / CPB2;
+};
+
 template <int N>
 __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
     using L = FastLayout<N>;
+    using P = PairLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
-    constexpr int CPB1 = kFastWarps * PPW;
-    constexpr int CBLK = (N + CPB1 - 1) / CPB1;
     constexpr int ROWS = N / 2 + 1;
     constexpr int64_t NN = (int64_t)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -285,37 +323,30 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
     __syncthreads();
     const int64_t blk = blockIdx.x;
-    const int64_t pr = blk / (ROWS * CBLK);
-    const int rem = (int)(blk - pr * ROWS * CBLK);
-    const int l = rem / CBLK, cb = rem % CBLK;
+    const int64_t pr = blk / (ROWS * P::CBLK);
+    const int rem = (int)(blk - pr * ROWS * P::CBLK);
+    const int l = rem / P::CBLK, cb = rem % P::CBLK;
     const int qlim = 2 * l == N ? N / 2 : N;
-    const int cw = cb * CPB1 + warp * PPW;
-    if (cw >= qlim) return;   // warp-uniform; no block barrier below
+    const bool partner = warp >= kFastWarps / 2;
+    const int wq = partner ? warp - kFastWarps / 2 : warp;
     const int cl = lane % PPW, j = lane / PPW;
-    const int c = cw + cl;
-    const bool act = c < qlim;
-    const int lp = (N - l) % N;
-    const int cp = (c - l + N) % N;
+    const int c = cb * P::CPB2 + wq * PPW + cl;                     // primary column
+    // warp-uniform: the whole primary warp is past the end, or row 0's partner warps
+    const bool idle = cb * P::CPB2 + wq * PPW >= qlim || (partner && l == 0);
+    const bool act = !idle && c < qlim;
+    const int lo = partner ? (N - l) % N : l;
+    const int co = partner ? (c - l + N) % N : c;
+    const int64_t base = pr * vstride + (int64_t)lo * N + co;     // own pencil; + k * NN
     float2* ex = exall + warp * L::EXW + cl * L::EXP;
-    const int64_t vb = pr * vstride;
-    const int64_t ba = vb + (int64_t)l * N + c;     // own pencil; + k * NN
-    const int64_t bp = vb + (int64_t)lp * N + cp;   // partner pencil
-    float ar[R1], ai[R1], br[R1], bi[R1];
+    float ur[E][G], ui[E][G];
+    if (!idle) {
+        float vr[R1], vi[R1];
 #pragma unroll
-    for (int m = 0; m < R1; ++m) {
-        const int64_t o = (int64_t)(j + G * m) * NN;
-        const float2 t = act ? in[ba + o] : make_float2(0.f, 0.f);
-        const float2 u = act ? in[bp + o] : make_float2(0.f, 0.f);
-        ar[m] = t.x;
-        ai[m] = t.y;
-        br[m] = u.x;
-        bi[m] = u.y;
-    }
-    float ur[2][E][G], ui[2][E][G];
-#pragma unroll
-    for (int pz = 0; pz < 2; ++pz) {
-        float* vr = pz ? br : ar;
-        float* vi = pz ? bi : ai;
+        for (int m = 0; m < R1; ++m) {
+            const float2 t = act ? in[base + (int64_t)(j + G * m) * NN] : make_float2(0.f, 0.f);
+            vr[m] = t.x;
+            vi[m] = t.y;
+        }
         pencil_stage1<N, 1>(vr, vi, j, ex, tw);
         __syncwarp();
 #pragma unroll
@@ -323,36 +354,36 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
 #pragma unroll
             for (int jj = 0; jj < G; ++jj) {
                 const float2 t = ex[jj * (R1 + 1) + j + G * e];
-                ur[pz][e][jj] = t.x;
-                ui[pz][e][jj] = t.y;
+                ur[e][jj] = t.x;
+                ui[e][jj] = t.y;
             }
         }
         __syncwarp();
-    }
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        reg::Dft<G, 1, float>::run(ur[0][e], ui[0][e]);
-        reg::Dft<G, 1, float>::run(ur[1][e], ui[1][e]);
+        for (int e = 0; e < E; ++e) {
+            reg::Dft<G, 1, float>::run(ur[e], ui[e]);
 #pragma unroll
-        for (int k1 = 0; k1 < G; ++k1) ex[j + G * e + R1 * k1] = make_float2(ur[1][e][k1], ui[1][e][k1]);
+            for (int k1 = 0; k1 < G; ++k1) ex[j + G * e + R1 * k1] = make_float2(ur[e][k1], ui[e][k1]);
+        }
     }
-    __syncwarp();
+    __syncthreads();
+    if (idle) return;
+    // counterpart pencil: the other half of the block, same slot (row 0: itself)
+    const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXP;
+    const int sh = partner ? l : N - l;   // k' = k - l (primary) or k + l (partner), mod N
 #pragma unroll
     for (int e = 0; e < E; ++e) {
 #pragma unroll
         for (int k1 = 0; k1 < G; ++k1) {
             const int k = j + G * e + R1 * k1;
-            int kp = k - l;
-            kp += kp < 0 ? N : 0;
-            const float2 B = ex[kp];
-            const float Ar = ur[0][e][k1], Ai = ui[0][e][k1];
-            const float2 y1 = make_float2(0.5f * (Ar + B.x), 0.5f * (Ai - B.y));
+            int kc = k + sh;
+            kc -= kc >= N ? N : 0;
+            const float2 B = cx[kc];
+            const float Ar = ur[e][k1], Ai = ui[e][k1];
             const float dr = 0.5f * (Ar - B.x), di = 0.5f * (Ai + B.y);   // y2 = -i d
             if (act) {
-                out[ba + k * NN] = y1;
-                out[ba + N3 + k * NN] = make_float2(di, -dr);
-                out[bp + kp * NN] = make_float2(y1.x, -y1.y);
-                out[bp + N3 + kp * NN] = make_float2(di, dr);
+                out[base + k * NN] = make_float2(0.5f * (Ar + B.x), 0.5f * (Ai - B.y));
+                out[base + N3 + k * NN] = make_float2(di, -dr);
             }
         }
     }

@@ -17,13 +17,17 @@
 // or imaginary part), C (96 x K) the core image with row 4g + p: output slot
 // g, part p = A1 re, A1 im, A2 re, A2 im.  Both operands are K-major without
 // swizzle: 8-row x 16-byte core matrices, LBO = 128 bytes between core
-// matrices along K, SBO between 8-row groups.  Thread t owns orbit t of the
-// block's tile: it writes row t of X and reads TMEM lane t in the epilogue,
-// so no transpose is needed anywhere.
+// matrices along K, SBO between 8-row groups.  Threads t and t + 128 own
+// orbit t of the block's tile, slots 0-11 and 12-23: each writes its half of
+// row t of X and reads its half of TMEM lane t in the epilogue, so no
+// transpose is needed anywhere.
 //
 // Pipeline per block (4 warps = 4 tiles of the plan, <= 128 orbits): the
-// gather loads of the next tile are issued right after the MMAs of the
-// current one and are in flight during its completion wait and epilogue.
+// gather loads of the next tile are issued as soon as the current tile's data
+// operand is stored, so they are in flight during the barrier, the MMAs, the
+// completion wait and the epilogue.  Representatives come from a table
+// padded to 32 per plan tile (all ones = no orbit), read a tile ahead, so no
+// chain of dependent table loads precedes the gather.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -38,7 +42,7 @@
 
 namespace fcc {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two threads per orbit: slots 0-11 and 12-23
 constexpr int kTcK = 48;                       // real inputs per orbit
 constexpr uint32_t kTcWaitLimit = 1u << 26;    // bounded mbarrier wait
 
@@ -57,7 +61,7 @@ struct TcLayout {
     static constexpr size_t smem = CMAT + (size_t)TERMS * XMAT + 64;
     static constexpr uint32_t idesc = (1u << 4) | ((KIND == 0 ? 1u : 2u) << 7) | ((KIND == 0 ? 1u : 2u) << 10) |
                                       ((uint32_t)(NOUT >> 3) << 17) | ((128u >> 4) << 24);
-    static constexpr int blocks_per_sm = KIND == 0 ? 4 : 3;   // shared memory; TMEM allows 4
+    static constexpr int blocks_per_sm = KIND == 0 ? 4 : 3;   // TMEM allows 4; TF32: shared memory
     // byte offset of element (row r, k) inside one operand
     __host__ __device__ static constexpr uint32_t off(int r, int k) {
         return (uint32_t)((r / 8) * SBO + (k / KE) * LBO + (r % 8) * 16 + (k % KE) * ES);
@@ -80,14 +84,14 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(u);
 }
 
-// Row `row` of the data operand: the split of the 48 inputs of one orbit,
-// 16 bytes (one core-matrix row) per store.
-template <int KIND>
-__device__ __forceinline__ void store_row(unsigned char* X, int row, const float* vr, const float* vi) {
+// Slots H .. H + 11 of row `row` of the data operand: the split of 24 inputs
+// of one orbit, 16 bytes (one core-matrix row) per store.
+template <int KIND, int H>
+__device__ __forceinline__ void store_half(unsigned char* X, int row, const float* vr, const float* vi) {
     using L = TcLayout<KIND>;
     if (KIND == 0) {
 #pragma unroll
-        for (int c = 0; c < kTcK / 8; ++c) {   // slots 4c .. 4c + 3
+        for (int c = 0; c < 3; ++c) {   // slots H + 4c .. H + 4c + 3
             float r[8];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -106,27 +110,73 @@ __device__ __forceinline__ void store_row(unsigned char* X, int row, const float
                         r[2 * e + 1] -= __high2float(h);
                     }
                 }
-                *reinterpret_cast<uint4*>(X + t * L::XMAT + L::off(row, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(X + t * L::XMAT + L::off(row, 2 * H + 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < kTcK / 4; ++c) {   // slots 2c, 2c + 1
+        for (int c = 0; c < 6; ++c) {   // slots H + 2c, H + 2c + 1
             const float r0 = vr[2 * c], i0 = vi[2 * c], r1 = vr[2 * c + 1], i1 = vi[2 * c + 1];
             const float hr0 = tf32_round(r0), hi0 = tf32_round(i0), hr1 = tf32_round(r1), hi1 = tf32_round(i1);
-            *reinterpret_cast<float4*>(X + L::off(row, 4 * c)) = make_float4(hr0, hi0, hr1, hi1);
-            *reinterpret_cast<float4*>(X + L::XMAT + L::off(row, 4 * c)) =
+            *reinterpret_cast<float4*>(X + L::off(row, 2 * H + 4 * c)) = make_float4(hr0, hi0, hr1, hi1);
+            *reinterpret_cast<float4*>(X + L::XMAT + L::off(row, 2 * H + 4 * c)) =
                 make_float4(tf32_round(r0 - hr0), tf32_round(i0 - hi0), tf32_round(r1 - hr1), tf32_round(i1 - hi1));
         }
     }
 }
 
+// Loads of slots H .. H + 11 of representative rp (both volumes of the pair).
+template <int H>
+__device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* in0, const float* in1, uint32_t rp,
+                                            float* vr, float* vi) {
+    const bool act = rp != 0xffffffffu;
+    static_for<0, 12>([&](auto Sc) {
+        constexpr int g = H + decltype(Sc)::value;
+        const int gi = act ? rep_dot(rp, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3] : 0;
+        vr[g - H] = act ? __ldg(in0 + gi) : 0.f;
+        vi[g - H] = act ? __ldg(in1 + gi) : 0.f;
+    });
+}
+
+// Epilogue for slots H .. H + 11 of this thread's orbit: TMEM columns 4H ..
+// 4H + 47 of lane trow, A1 + A2 / sqrt 2, row phase R_g / 24, scatter.
+template <int H>
+__device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t trow, uint32_t rep, float2* out,
+                                              int64_t pb, int M8) {
+    const float rs2 = 0.70710678118654752440f;
+    const float sc = 1.0f / 24.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+              "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(trow + (uint32_t)(4 * H + 16 * c)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (rep != 0xffffffffu) {
+            static_for<0, 4>([&](auto Sc) {
+                constexpr int s4 = decltype(Sc)::value;
+                const int g = H + 4 * c + s4;
+                const float re = fmaf(__uint_as_float(v[4 * s4 + 2]), rs2, __uint_as_float(v[4 * s4]));
+                const float im = fmaf(__uint_as_float(v[4 * s4 + 3]), rs2, __uint_as_float(v[4 * s4 + 1]));
+                int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
+                q = q < 0 ? q + M8 : q;
+                const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
+                const float2 R = __ldg(a.phase + q);
+                out[pb + gi] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
+            });
+        }
+    }
+}
+
 // grid.x: blocks looping over groups of 4 free tiles; grid.y: pairs of real volumes.
+// reps32: representatives of the free tiles, 32 per tile, 0xffffffff = none.
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
-                       const uint4* __restrict__ core_image, int* status) {
+                       const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* Cs = smem_raw;                 // core, 96 x 48
@@ -135,9 +185,9 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bar + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & 127, half = tid >> 7, wq = warp & 3;   // orbit row; slot half; TMEM lane quarter
     const int n = a.n, M8 = 8 * n;
     const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;
-    const float2* __restrict__ ph = a.phase;
 
     for (int e = tid; e < (int)(L::core_bytes / 16); e += kTcThreads)
         reinterpret_cast<uint4*>(Cs)[e] = core_image[e];
@@ -153,41 +203,38 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *s_tmem;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
+    const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16);   // this warp's TMEM lanes
 
-    const float rs2 = 0.70710678118654752440f;
-    const float sc = 1.0f / 24.0f;
     const int ngroups = (nfree_tiles + 3) / 4;
     uint32_t phase = 0;
     bool ok = true;
 
-    // gather of one tile into registers: thread = orbit, all 48 loads in flight
-    float vr[24], vi[24];
-    uint32_t nrep = 0;
-    bool nact = false;
-    auto gather = [&](int grp) {
-        const int tile = grp * 4 + warp;
-        int o0 = 0, cnt = 0;
-        if (tile < nfree_tiles) {
-            o0 = __ldg(a.tile_off + tile);
-            cnt = __ldg(a.tile_off + tile + 1) - o0;
-        }
-        nact = lane < cnt;
-        nrep = nact ? __ldg(a.reps + o0 + lane) : 0u;
-        static_for<0, 24>([&](auto Gc) {
-            constexpr int g = decltype(Gc)::value;
-            const int gi = rep_dot(nrep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
-            vr[g] = nact ? __ldg(in + pb + gi) : 0.f;
-            vi[g] = nact ? __ldg(in + pb + a.n3 + gi) : 0.f;
-        });
+    // gather of one tile into registers: two threads per orbit, 24 loads each in flight
+    const uint32_t kNone = 0xffffffffu;
+    const float* __restrict__ in0 = in + pb;
+    const float* __restrict__ in1 = in + pb + a.n3;
+    auto rep_of = [&](int g) -> uint32_t {
+        const int tile = g * 4 + wq;
+        return (g < ngroups && tile < nfree_tiles) ? __ldg(reps32 + (size_t)tile * 32 + lane) : kNone;
+    };
+    float vr[12], vi[12];
+    auto gather = [&](uint32_t rp) {   // warp-uniform branch on the slot half
+        if (half == 0) gather_half<0>(a, in0, in1, rp, vr, vi);
+        else gather_half<12>(a, in0, in1, rp, vr, vi);
     };
 
+    const int gstep = (int)gridDim.x;
     int grp = blockIdx.x;
-    if (grp < ngroups) gather(grp);
-    for (; grp < ngroups && ok; grp += gridDim.x) {
-        const uint32_t rep = nrep;
-        const bool act = nact;
-        store_row<KIND>(Xs, tid, vr, vi);
+    uint32_t rcur = rep_of(grp), rnext = rep_of(grp + gstep);
+    if (grp < ngroups) gather(rcur);
+    for (; grp < ngroups && ok; grp += gstep) {
+        const uint32_t rep = rcur;
+        if (half == 0) store_half<KIND, 0>(Xs, row, vr, vi);
+        else store_half<KIND, 12>(Xs, row, vr, vi);
+        // the next tile's loads overlap the barrier, the MMAs, the wait and the epilogue
+        rcur = rnext;
+        if (grp + gstep < ngroups) gather(rcur);
+        rnext = rep_of(grp + 2 * gstep);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -212,9 +259,6 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
         }
-        // the next tile's loads overlap the MMAs, the wait and this epilogue
-        const int nxt = grp + (int)gridDim.x;
-        if (nxt < ngroups) gather(nxt);
         uint32_t done = 0;
         for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
             asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -228,35 +272,9 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
             ok = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ok) {
-            // epilogue: TMEM lane = this thread's orbit; 32 columns = 8 slots per load
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uint32_t v[32];
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                      "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                      "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(trow + (uint32_t)(32 * c)));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                static_for<0, 8>([&](auto Sc) {
-                    constexpr int s8 = decltype(Sc)::value;
-                    const int g = 8 * c + s8;
-                    const float re = fmaf(__uint_as_float(v[4 * s8 + 2]), rs2, __uint_as_float(v[4 * s8]));
-                    const float im = fmaf(__uint_as_float(v[4 * s8 + 3]), rs2, __uint_as_float(v[4 * s8 + 1]));
-                    int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
-                    q = q < 0 ? q + M8 : q;
-                    const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
-                    if (act) {
-                        const float2 R = __ldg(ph + q);
-                        reinterpret_cast<float2*>(out)[pb + gi] =
-                            make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
-                    }
-                });
-            }
+        if (ok) {   // warp-uniform: tcgen05.ld is executed by whole warps
+            if (half == 0) epilogue_half<0>(a, trow, rep, reinterpret_cast<float2*>(out), pb, M8);
+            else epilogue_half<12>(a, trow, rep, reinterpret_cast<float2*>(out), pb, M8);
         }
         // TMEM reads complete before the next tile's MMAs (issued after the next barrier)
         asm volatile("tcgen05.fence::before_thread_sync;");
