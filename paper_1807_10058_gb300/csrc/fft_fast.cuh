@@ -42,14 +42,25 @@ FCC_SHAPE(8, 4, 2)
 constexpr int kFastThreads = 256;            // pencil kernel
 constexpr int kFastWarps = kFastThreads / 32;
 
+// Smallest stride >= e at which the 8-byte exchange accesses of the pencil
+// layout are free of bank conflicts: PPW = 32 / g pencils per warp must land
+// 32 / PPW banks apart within a 16-lane phase.
+constexpr int pencil_stride(int g, int e) {
+    while (!(g == 8 ? (e % 16 == 4 || e % 16 == 12) : g == 4 ? e % 4 == 2 : g == 2 ? e % 2 == 1 : true)) ++e;
+    return e;
+}
+
 template <int N>
 struct FastLayout {
     static constexpr int R1 = FftShape<N>::R1;
     static constexpr int G = FftShape<N>::G;
     static constexpr int PPW = 32 / G;                 // pencils per warp
     static constexpr int LD = N + 4;                   // slab row stride (complex)
-    static constexpr int EXP = G * (R1 + 1);           // exchange stride per pencil
-    static constexpr int EXW = PPW * EXP;              // exchange per warp
+    static constexpr int EXP = G * (R1 + 1);           // exchange stride per pencil (lane = p G + j)
+    // stride for the pencil layout (lane = j PPW + cl): padded so that the
+    // PPW pencils of a half-warp fall into distinct shared-memory banks
+    static constexpr int EXPC = pencil_stride(G, EXP);
+    static constexpr int EXW = PPW * EXPC;             // exchange per warp
     // slab kernel: 16 warps when the slab and 16 exchange buffers fit in
     // ~200 KB (leaving room on the SM for a block of another kernel)
     static constexpr int SW = ((size_t)(N * LD + 16 * EXW + N) * 8 <= 200 * 1024) ? 16 : 8;
@@ -186,7 +197,7 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, i
     // columns (middle axis), results straight to global memory
     {
         const int cl = lane % PPW, j = lane / PPW;
-        float2* ex = exall + warp * L::EXW + cl * L::EXP;
+        float2* ex = exall + warp * L::EXW + cl * L::EXPC;
         for (int c0 = 0; c0 < N; c0 += SW * PPW) {
             if (c0 + warp * PPW >= N) continue;   // warp-uniform
             const int c = c0 + warp * PPW + cl;
@@ -229,7 +240,7 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg,
     if (cb * CPB + NP * warp * PPW >= N) return;   // warp-uniform; no block barrier below
     const int c = cb * CPB + NP * (warp * PPW + cl);
     const bool act = c < N;
-    float2* ex = exall + warp * L::EXW + cl * L::EXP;
+    float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     const int64_t NN = (int64_t)N * N;
     const int64_t base = vol_base(voff, vol, vstride) + (int64_t)b * N + c;
     float ar[R1], ai[R1], br[R1], bi[R1];
@@ -337,7 +348,7 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     const int lo = partner ? (N - l) % N : l;
     const int co = partner ? (c - l + N) % N : c;
     const int64_t base = pr * vstride + (int64_t)lo * N + co;     // own pencil; + k * NN
-    float2* ex = exall + warp * L::EXW + cl * L::EXP;
+    float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     float ur[E][G], ui[E][G];
     if (!idle) {
         float vr[R1], vi[R1];
@@ -369,7 +380,7 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     __syncthreads();
     if (idle) return;
     // counterpart pencil: the other half of the block, same slot (row 0: itself)
-    const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXP;
+    const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXPC;
     const int sh = partner ? l : N - l;   // k' = k - l (primary) or k + l (partner), mod N
 #pragma unroll
     for (int e = 0; e < E; ++e) {
