@@ -226,9 +226,9 @@ def _time(fn, steps, warmup):
 
 def secondary_configs(dev):
     """The other workloads, each short: order 64 x 256 round trip; a ragged
-    batch of 1000 volumes (orders 8..96) grouped by order in a CUDA graph vs
-    one launch set per volume; order 96 x 32 masked-reconstruction gradient
-    descent through the autograd wrapper."""
+    batch of 1000 volumes (orders 8..96) under each ragged schedule; order
+    96 x 32 masked-reconstruction gradient descent through the autograd
+    wrapper."""
     import numpy as np
     import torch
     from paper_1807_10058_gb300 import binding, inputs
@@ -244,12 +244,15 @@ def secondary_configs(dev):
         rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
     out["roundtrip_n64_b256"] = {"value": b * n ** 3 / (ms * 1e-3) / 1e9, "unit": "Gpoints/s (forward + inverse)",
                                  "ms_per_step": ms, "roundtrip_rel_l2": rt, "data": "i.i.d. N(0,1) coefficients"}
-    # ragged, 1000 volumes
+    # ragged, 1000 volumes: per-order launches and the single persistent
+    # launch, each captured in a CUDA graph; one launch set per run of equal
+    # orders (no graph); then the autotuner's pick
     orders = inputs.ragged_orders(1000, seed=0)
     tot = sum(o ** 3 for o in orders)
     x = torch.randn(tot, device=dev)
     y = torch.empty(tot, dtype=torch.complex64, device=dev)
-    with binding.Plan(orders=orders, dtype="r32") as p:
+
+    def graph_ms(p):
         p.forward(x, out=y)
         torch.cuda.synchronize()
         s = torch.cuda.Stream()
@@ -258,21 +261,25 @@ def secondary_configs(dev):
         with torch.cuda.graph(g, stream=s):
             p.forward(x, out=y)
         torch.cuda.current_stream().wait_stream(s)
-        ms_graph = _time(g.replay, 5, 2)
+        return _time(g.replay, 5, 2)
+
+    rag = {"points": tot, "unit": "Gpoints/s", "data": "i.i.d. N(0,1) coefficients, orders U{8..96}"}
+    with binding.Plan(orders=orders, dtype="r32") as p:
+        ms = graph_ms(p)
         ref = y.clone()
-        launches = p.launches(0)
-    os.environ["FCC_RAGGED_GROUPED"] = "0"
-    try:
-        with binding.Plan(orders=orders, dtype="r32") as q:
-            ms_per = _time(lambda: q.forward(x, out=y), 3, 1)
-            launches_per = q.launches(0)
-            same = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
-    finally:
-        del os.environ["FCC_RAGGED_GROUPED"]
-    out["ragged_1000"] = {"points": tot, "grouped_graph": {"value": tot / (ms_graph * 1e-3) / 1e9, "ms": ms_graph,
-                                                            "launches": launches},
-                          "per_volume": {"value": tot / (ms_per * 1e-3) / 1e9, "ms": ms_per, "launches": launches_per},
-                          "unit": "Gpoints/s", "rel_diff": same, "data": "i.i.d. N(0,1) coefficients, orders U{8..96}"}
+        rag["grouped_graph"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(0)}
+        p.set_schedule(ragged=1)
+        ms = graph_ms(p)
+        diff = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
+        rag["persistent_graph"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(0),
+                                   "rel_diff": diff}
+        p.set_schedule(ragged=2)
+        ms = _time(lambda: p.forward(x, out=y), 3, 1)
+        diff = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
+        rag["per_volume"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(0), "rel_diff": diff}
+        ms, sched = p.autotune(x, y, reps=2)
+        rag["autotuned"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "schedule": sched, "launches": p.launches(0)}
+    out["ragged_1000"] = rag
     # autograd: 50 gradient-descent steps of ||M . (D x) - b||^2, n = 96, batch 32
     n, b = 96, 32
     xt = inputs.phantom_device(n, b, seed=9, device=dev)

@@ -171,6 +171,50 @@ fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, voi
  */
 fcc_status fcc_dct_check(fcc_plan* plan);
 
+/*
+ * Execution schedule.  The paper has no counterpart: these knobs change only
+ * how the plan's work is laid out on the GPU (the results agree to FP32
+ * rounding order).  Keys and values:
+ *   FCC_SCHED_CHUNK_MB   1..1024   MB of complex intermediate per chunk of
+ *                                  volumes (kept L2-resident between passes);
+ *                                  inverse / adjoint chunks stay within the
+ *                                  workspace sized at plan creation
+ *   FCC_SCHED_STREAMS    1..4      internal streams the chunks alternate over
+ *                                  (inverse / adjoint: at most the count at
+ *                                  plan creation)
+ *   FCC_SCHED_RAGGED     0, 1, 2   ragged FP32 forward: 0 = one mixing, slab and
+ *                                  pencil launch per distinct order; 1 = the
+ *                                  whole batch in one persistent cooperative
+ *                                  launch (orders with a register-radix DFT,
+ *                                  at most 16 distinct orders, else
+ *                                  FCC_ERR_UNSUPPORTED); 2 = one launch set per
+ *                                  run of equal orders
+ *   FCC_SCHED_TC_BLOCKS  0..4      tensor-core mixing: blocks per SM in the
+ *                                  grid (0 = as many as can be resident)
+ * set_schedule returns FCC_ERR_INVALID_ARG for an unknown key or a value out
+ * of range; get_schedule returns the current value, or -1 on a bad argument.
+ */
+typedef enum {
+    FCC_SCHED_CHUNK_MB = 0,
+    FCC_SCHED_STREAMS = 1,
+    FCC_SCHED_RAGGED = 2,
+    FCC_SCHED_TC_BLOCKS = 3
+} fcc_sched_key;
+fcc_status fcc_dct_set_schedule(fcc_plan* plan, int key, int value);
+int fcc_dct_get_schedule(const fcc_plan* plan, int key);
+
+/*
+ * Autotuner (no counterpart in the paper): times the forward transform of
+ * `in` into `out` (device buffers, the layouts of fcc_dct_forward) under the
+ * candidate schedules -- chunk size x internal streams and the tensor-core
+ * grid for uniform plans; per-order launches x streams, the persistent
+ * launch and per-run launches for ragged plans -- with one untimed call and
+ * `reps` (1..100) timed calls each, keeps the fastest and writes its time per
+ * call to *best_ms (if not NULL).  Synchronises `stream`; overwrites `out`.
+ * Candidates the device refuses are skipped.
+ */
+fcc_status fcc_dct_autotune(fcc_plan* plan, const void* in, void* out, void* stream, int reps, float* best_ms);
+
 /* Status of the last failing call on this host thread (FCC_OK if none). */
 fcc_status fcc_dct_last_error(void);
 const char* fcc_status_string(fcc_status status);

@@ -21,7 +21,11 @@ EXPORTS = [
     "fcc_dct_in_bytes", "fcc_dct_out_bytes", "fcc_dct_launches", "fcc_dct_last_error",
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
     "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
+    "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune",
 ]
+
+# execution-schedule keys (fcc_sched_key)
+SCHED = {"chunk_mb": 0, "streams": 1, "ragged": 2, "tc_blocks": 3}
 
 _LIB = None
 
@@ -72,6 +76,12 @@ def lib():
         L.fcc_dct_profile_enable.restype = i32
         L.fcc_dct_profile_read.argtypes = [vp, vp, vp, vp, i32]
         L.fcc_dct_profile_read.restype = i32
+        L.fcc_dct_set_schedule.argtypes = [vp, i32, i32]
+        L.fcc_dct_set_schedule.restype = i32
+        L.fcc_dct_get_schedule.argtypes = [vp, i32]
+        L.fcc_dct_get_schedule.restype = i32
+        L.fcc_dct_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float)]
+        L.fcc_dct_autotune.restype = i32
         _LIB = L
     return _LIB
 
@@ -165,6 +175,25 @@ class Plan:
 
     def launches(self, which=0):
         return lib().fcc_dct_launches(self.handle, which)
+
+    def set_schedule(self, **kw):
+        """Execution schedule knobs: chunk_mb, streams, ragged (0 per-order
+        launches, 1 one persistent launch, 2 per run of equal orders), tc_blocks."""
+        for k, v in kw.items():
+            _check(lib().fcc_dct_set_schedule(self.handle, SCHED[k], int(v)), "set_schedule(%s)" % k)
+
+    def schedule(self):
+        return {k: lib().fcc_dct_get_schedule(self.handle, v) for k, v in SCHED.items()}
+
+    def autotune(self, x, out, reps=3):
+        """Time the forward transform under the candidate schedules, keep the
+        fastest; returns (ms per call, schedule).  Synchronises the stream."""
+        import torch
+        best = ctypes.c_float(0.0)
+        st = torch.cuda.current_stream().cuda_stream
+        _check(lib().fcc_dct_autotune(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(st), int(reps), ctypes.byref(best)), "autotune")
+        return best.value, self.schedule()
 
     def profile(self, enable=True):
         _check(lib().fcc_dct_profile_enable(self.handle, 1 if enable else 0), "profile_enable")

@@ -17,6 +17,7 @@
 #include "fft_fast.cuh"
 #include "kernels.cuh"
 #include "mix_tc.cuh"
+#include "ragged.cuh"
 #include "mix_tiled.cuh"
 #include "pair.cuh"
 #include "plan.h"
@@ -91,6 +92,9 @@ struct fcc_plan {
     int nstreams = 2;
     bool pairing = true;             // real dtypes: two volumes per complex transform
     bool ragged_fast = true;         // ragged FP32 forward: per-order launches over offset tables
+    int ragged_mode = 0;             // FCC_SCHED_RAGGED: 0 per-order launches, 1 one persistent launch, 2 per run of volumes
+    int tc_blocks = 0;               // FCC_SCHED_TC_BLOCKS: tensor-core mixing blocks per SM in the grid (0 = resident maximum)
+    int scratch_streams = 1;         // internal streams the inverse / adjoint workspace was sized for
     int num_sms = 1;
     int* d_status = nullptr;         // device-side wait timeouts (tensor-core kernels)
     cudaStream_t streams[kMaxStreams] = {};
@@ -214,6 +218,9 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
             core[1152 + e] = make_float2((float)oc.adj[e].real(), (float)oc.adj[e].imag());
         }
         if (cudaMemcpyToSymbol(c_core, core.data(), core.size() * sizeof(float2)) != cudaSuccess) return FCC_ERR_CUDA;
+        // the persistent ragged kernel's translation unit holds its own copies
+        const WeylGroup& G = weyl();
+        if (ragged_upload_constants(core.data(), &G.m[0][0], &G.u[0][0]) != cudaSuccess) return FCC_ERR_CUDA;
     }
     return FCC_OK;
 }
@@ -309,7 +316,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         if (const char* e = std::getenv("FCC_STREAMS")) p->nstreams = std::min(kMaxStreams, std::max(1, std::atoi(e)));
         if (const char* e = std::getenv("FCC_PAIRING")) p->pairing = std::atoi(e) != 0;
         if (const char* e = std::getenv("FCC_RAGGED_GROUPED")) p->ragged_fast = std::atoi(e) != 0;
-        for (int i = 0; i < p->nstreams && s == FCC_OK; ++i) {
+        for (int i = 0; i < kMaxStreams && s == FCC_OK; ++i) {
             if (cudaStreamCreateWithFlags(&p->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
                 s = FCC_ERR_CUDA;
@@ -325,6 +332,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         int64_t chunk_pts = std::max<int64_t>(maxpts, p->chunk_bytes / bytes_per_pt);
         chunk_pts = std::min<int64_t>(chunk_pts, p->points);
         p->scratch_points = chunk_pts;
+        p->scratch_streams = p->nstreams;
         s = dev_alloc(p, &p->scratch, chunk_pts * bytes_per_pt * p->nstreams);
     }
     if (s != FCC_OK) {
@@ -468,9 +476,7 @@ void set_mix_tiled_attributes() {
 }
 
 // which: 0 = every tile, 1 = free tiles only, 2 = boundary tiles only
-fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
-                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false, int which = 0,
-                            const int64_t* voff = nullptr) {
+TiledMixArgs make_mix_args(const OrderTables& t, int mode, float scale) {
     TiledMixArgs a;
     a.tile_off = t.tile_off;
     a.reps = t.tile_reps;
@@ -482,18 +488,23 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
     a.canon_mask = t.canon_mask;
     a.phase = (const float2*)t.phase;
     a.n = t.n;
-    {
-        const int n = t.n;
-        for (int g = 0; g < 24; ++g) {
-            for (int j = 0; j < 3; ++j)
-                a.lin[g][j] = wc::K::t.m[g][j] * n * n + wc::K::t.m[g][3 + j] * n + wc::K::t.m[g][6 + j];
-            a.lin[g][3] = -n * (wc::K::t.fw[g][0] * n * n + wc::K::t.fw[g][1] * n + wc::K::t.fw[g][2]);
-        }
+    const int n = t.n;
+    for (int g = 0; g < 24; ++g) {
+        for (int j = 0; j < 3; ++j)
+            a.lin[g][j] = wc::K::t.m[g][j] * n * n + wc::K::t.m[g][3 + j] * n + wc::K::t.m[g][6 + j];
+        a.lin[g][3] = -n * (wc::K::t.fw[g][0] * n * n + wc::K::t.fw[g][1] * n + wc::K::t.fw[g][2]);
     }
     a.ncls = t.n_classes;
     a.free_class = t.free_class;
     a.n3 = (int64_t)t.n * t.n * t.n;
     a.scale = scale;
+    return a;
+}
+
+fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool real_out, const float* in,
+                            float* out, int64_t nvol, float scale, cudaStream_t st, bool pair = false, int which = 0,
+                            const int64_t* voff = nullptr) {
+    TiledMixArgs a = make_mix_args(t, mode, scale);
     if (t.n_classes > kMaxClasses) return FCC_ERR_UNSUPPORTED;
     const size_t smem = mix_tiled_smem(t.n);
     set_mix_tiled_attributes();
@@ -616,27 +627,7 @@ fcc_status dft3_split_pairs(const OrderTables& t, float* y, int64_t np, cudaStre
 // tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
                                cudaStream_t st) {
-    TiledMixArgs a;
-    a.tile_off = t.tile_off;
-    a.reps = t.tile_reps;
-    a.cls = t.tile_cls;
-    a.permb = t.tile_pb;
-    a.permc = t.tile_pc;
-    a.mats = (const float*)t.mat[MODE_FWD];
-    a.wrap = t.wrap;
-    a.canon_mask = t.canon_mask;
-    a.phase = (const float2*)t.phase;
-    a.n = t.n;
-    for (int g = 0; g < 24; ++g) {
-        const int n = t.n;
-        for (int j = 0; j < 3; ++j)
-            a.lin[g][j] = wc::K::t.m[g][j] * n * n + wc::K::t.m[g][3 + j] * n + wc::K::t.m[g][6 + j];
-        a.lin[g][3] = -n * (wc::K::t.fw[g][0] * n * n + wc::K::t.fw[g][1] * n + wc::K::t.fw[g][2]);
-    }
-    a.ncls = t.n_classes;
-    a.free_class = t.free_class;
-    a.n3 = (int64_t)t.n * t.n * t.n;
-    a.scale = 1.f;
+    TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
     const bool bf16 = p->dtype == FCC_R32_BF16X3;
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
     set_mix_tiled_attributes();
@@ -652,7 +643,8 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
         float* dst = out + v0 * a.n3 * 4;
         if (t.free_tiles > 0 && t.tc_core_image) {
             const int ngroups = (t.free_tiles + 3) / 4;
-            const int per_sm = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
+            const int lim = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
+            const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, lim) : lim;
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);
@@ -685,7 +677,8 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     const bool rin = is_real_in(p->dtype);
     const int64_t n3 = (int64_t)t.n * t.n * t.n;
     const int64_t cv = std::min<int64_t>(chunk_vols(p, t.n), std::max<int64_t>(1, p->scratch_points / n3));
-    const int ns = p->nstreams;
+    // inverse / adjoint give each stream a slice of the workspace
+    const int ns = which == 0 ? p->nstreams : std::min(p->nstreams, p->scratch_streams);
     if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
     for (int i = 0; i < ns; ++i)
         if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
@@ -758,6 +751,46 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
         if (cudaStreamWaitEvent(st, p->bnd_join, 0) != cudaSuccess) return FCC_ERR_CUDA;
     }
     return s;
+}
+
+// Ragged FP32 forward in one cooperative launch (ragged.cuh): every order has
+// a register-radix DFT and even volume offsets; at most kRaggedMaxOrders orders.
+bool ragged_persistent_ok(const fcc_plan* p) {
+    if (p->tabs.size() > (size_t)kRaggedMaxOrders) return false;
+    for (const auto& kv : p->tabs)
+        if (!ragged_order_supported(kv.first) || kv.second.free_class < 0) return false;
+    return true;
+}
+
+fcc_status run_ragged_persistent(fcc_plan* p, const float* in, float* out, cudaStream_t st) {
+    RaggedArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.real_in = is_real_in(p->dtype) ? 1 : 0;
+    std::vector<int> ords;
+    int64_t first[3] = {0, 0, 0};
+    for (const auto& kv : p->tabs) {
+        const OrderTables& t = kv.second;
+        RaggedOrder& o = ra.o[ra.norders++];
+        o.mix = make_mix_args(t, MODE_FWD, 1.f);
+        o.ntiles = t.ntiles;
+        o.nvol = t.nvoff;
+        o.tw = (const float2*)t.tw;
+        o.voff = t.voff;
+        for (int k = 0; k < 3; ++k) {
+            o.first[k] = first[k];
+            first[k] += ragged_units(t.n, t.ntiles, t.nvoff, k);
+        }
+        ords.push_back(t.n);
+    }
+    for (int k = 0; k < 3; ++k) ra.units[k] = first[k];
+    const size_t smem = ragged_smem_for(ords.data(), (int)ords.size());
+    ProfScope ps("ragged_persistent", st);
+    const cudaError_t e = launch_ragged_persistent(ra, in, out, smem, 0, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FCC_ERR_CUDA;
+    }
+    return FCC_OK;
 }
 
 // Ragged FP32 forward: per distinct order, one mixing launch and one slab and
@@ -841,8 +874,11 @@ template <typename T>
 fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t st) {
     const T* in = (const T*)vin;
     T* out = (T*)vout;
-    if (sizeof(T) == 4 && p->ragged_fast && ragged_fast_ok(p, which))
+    if (sizeof(T) == 4 && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_ok(p, which)) {
+        if (p->ragged_mode == 1 && ragged_persistent_ok(p))
+            return run_ragged_persistent(p, (const float*)vin, (float*)vout, st);
         return run_ragged_fast(p, (const float*)vin, (float*)vout, st);
+    }
     const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
     fcc_status s = FCC_OK;
@@ -903,6 +939,123 @@ fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype) {
     return make_plan(std::vector<int>(orders, orders + count), dtype);
 }
 
+fcc_status fcc_dct_set_schedule(fcc_plan* p, int key, int value) {
+    if (!p) return fail(FCC_ERR_INVALID_ARG);
+    switch (key) {
+        case FCC_SCHED_CHUNK_MB:
+            if (value < 1 || value > 1024) return fail(FCC_ERR_INVALID_ARG);
+            p->chunk_bytes = (int64_t)value << 20;
+            return FCC_OK;
+        case FCC_SCHED_STREAMS:
+            if (value < 1 || value > kMaxStreams) return fail(FCC_ERR_INVALID_ARG);
+            p->nstreams = value;
+            return FCC_OK;
+        case FCC_SCHED_RAGGED:
+            if (value < 0 || value > 2) return fail(FCC_ERR_INVALID_ARG);
+            if (value == 1 && (p->uniform || !ragged_fast_ok(p, 0) || !ragged_persistent_ok(p))) return fail(FCC_ERR_UNSUPPORTED);
+            p->ragged_mode = value;
+            return FCC_OK;
+        case FCC_SCHED_TC_BLOCKS:
+            if (value < 0 || value > 4) return fail(FCC_ERR_INVALID_ARG);
+            p->tc_blocks = value;
+            return FCC_OK;
+        default:
+            return fail(FCC_ERR_INVALID_ARG);
+    }
+}
+
+int fcc_dct_get_schedule(const fcc_plan* p, int key) {
+    if (!p) return -1;
+    switch (key) {
+        case FCC_SCHED_CHUNK_MB: return (int)(p->chunk_bytes >> 20);
+        case FCC_SCHED_STREAMS: return p->nstreams;
+        case FCC_SCHED_RAGGED: return p->ragged_mode;
+        case FCC_SCHED_TC_BLOCKS: return p->tc_blocks;
+        default: return -1;
+    }
+}
+
+fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream, int reps, float* best_ms) {
+    if (!p || !in || !out || reps < 1 || reps > 100) return fail(FCC_ERR_INVALID_ARG);
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Cand { int chunk_mb, streams, ragged, tc; };
+    std::vector<Cand> cands;
+    const int tc0 = p->tc_blocks;
+    if (!p->uniform) {
+        const bool fast = !is_double(p->dtype) && ragged_fast_ok(p, 0);
+        for (int ns = 1; ns <= 3 && fast; ++ns) cands.push_back({32, ns, 0, tc0});
+        if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0});
+        cands.push_back({32, 2, 2, tc0});
+    } else {
+        for (int mb : {16, 32, 64})
+            for (int ns = 1; ns <= 3; ++ns) cands.push_back({mb, ns, 0, tc0});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return fail(FCC_ERR_CUDA);
+    }
+    const Cand saved = {(int)(p->chunk_bytes >> 20), p->nstreams, p->ragged_mode, p->tc_blocks};
+    auto apply = [&](const Cand& c) {
+        p->chunk_bytes = (int64_t)c.chunk_mb << 20;
+        p->nstreams = c.streams;
+        p->ragged_mode = c.ragged;
+        p->tc_blocks = c.tc;
+    };
+    auto time_it = [&](const Cand& c, float& ms) -> bool {
+        apply(c);
+        if (dispatch(p, 0, in, out, stream) != FCC_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+            if (dispatch(p, 0, in, out, stream) != FCC_OK) {
+                cudaStreamSynchronize(st);
+                cudaGetLastError();
+                return false;
+            }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        ms /= (float)reps;
+        return true;
+    };
+    Cand best = saved;
+    float best_t = -1.f;
+    for (const Cand& c : cands) {
+        float ms = 0.f;
+        if (time_it(c, ms) && (best_t < 0.f || ms < best_t)) {
+            best_t = ms;
+            best = c;
+        }
+    }
+    // tensor-core forms: then the grid of the mixing kernel
+    if (p->uniform && is_tc(p->dtype) && best_t >= 0.f) {
+        for (int tcb : {2, 3, 4}) {
+            Cand c = best;
+            c.tc = tcb;
+            float ms = 0.f;
+            if (time_it(c, ms) && ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_t < 0.f) {
+        apply(saved);
+        return fail(FCC_ERR_CUDA);
+    }
+    apply(best);
+    if (best_ms) *best_ms = best_t;
+    return FCC_OK;
+}
+
 fcc_status fcc_dct_forward(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 0, in, out, stream); }
 fcc_status fcc_dct_inverse(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 1, in, out, stream); }
 fcc_status fcc_dct_adjoint(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 2, in, out, stream); }
@@ -917,7 +1070,8 @@ int64_t fcc_dct_out_bytes(const fcc_plan* p) { return p ? out_bytes(p, 0) : 0; }
 int fcc_dct_launches(const fcc_plan* p, int which) {
     if (!p) return 0;
     int total = 0;
-    if (!is_double(p->dtype) && p->ragged_fast && ragged_fast_ok(p, which)) {
+    if (!is_double(p->dtype) && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_ok(p, which)) {
+        if (p->ragged_mode == 1 && ragged_persistent_ok(p)) return 1;
         for (const auto& kv : p->tabs) {
             const OrderTables& t = kv.second;
             total += (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0) + 2;
@@ -939,11 +1093,17 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
             const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
             const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
             const int64_t npairs = pairing ? nv / 2 : 0;
-            const int64_t pchunks = (npairs + cv - 1) / cv;
-            const int64_t dft_per_pchunk = has_fast_fft(n) ? 2 : 3 * cv;   // generic passes go volume by volume
+            // per paired chunk: mixing, then the DFT passes and the pair split /
+            // merge (the fast forward fuses the split into its pencil pass;
+            // generic passes over strided pairs go pair by pair)
             const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
-            if (split_b) total += 1 + (int)(pchunks * (1 + 1 + dft_per_pchunk));
-            else total += (int)(pchunks * (mixl + 1 + dft_per_pchunk));
+            if (split_b) total += 1;
+            for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
+                const int64_t np = std::min(cv, npairs - p0);
+                // (the inverse / adjoint merge into a compact workspace first)
+                const int64_t dft_pair = has_fast_fft(n) ? (which == 0 ? 2 : 3) : (which == 0 ? 3 * np + 1 : 4);
+                total += (int)((split_b ? 1 : mixl) + dft_pair);
+            }
             const int64_t rest = nv - 2 * npairs;
             total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
         } else if (which == 0) total += mix + 3;

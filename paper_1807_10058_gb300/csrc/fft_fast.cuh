@@ -126,21 +126,25 @@ __device__ __forceinline__ int64_t vol_base(const int64_t* voff, int64_t v, int6
     return voff ? voff[v] : v * vstride;
 }
 
-// grid.x = number of slabs (volumes * N); volume v starts at voff[v] (or
-// v * vstride) complex values; in and out may alias.
-template <int N, int S>
-__global__ void __launch_bounds__(FastLayout<N>::SLAB_THREADS, 1)
-fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff) {
+// Shared memory of the slab transform with SW warps.
+template <int N>
+constexpr size_t slab_smem_for(int sw) {
+    return (size_t)(N * FastLayout<N>::LD + sw * FastLayout<N>::EXW + N) * sizeof(float2);
+}
+
+// DFT along the two fast axes of the n x n slab starting at `base` (complex
+// values), by a block of SW warps; in and out may alias.
+template <int N, int S, int SW>
+__device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, const float2* __restrict__ twg,
+                                              int64_t base, unsigned char* smem_raw) {
     using L = FastLayout<N>;
-    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD, SW = L::SW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD;
     float2* slab = reinterpret_cast<float2*>(smem_raw);
     float2* exall = slab + N * LD;
     float2* tw = exall + SW * L::EXW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < N; t += L::SLAB_THREADS) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < N; t += 32 * SW) tw[t] = twg[t];
     __syncthreads();
-    const int64_t base = vol_base(voff, blockIdx.x / N, vstride) + (int64_t)(blockIdx.x % N) * N * N;
 
     // rows (fastest axis)
     {
@@ -217,32 +221,37 @@ fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, i
     }
 }
 
+// grid.x = number of slabs (volumes * N); volume v starts at voff[v] (or
+// v * vstride) complex values; in and out may alias.
+template <int N, int S>
+__global__ void __launch_bounds__(FastLayout<N>::SLAB_THREADS, 1)
+fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t base = vol_base(voff, blockIdx.x / N, vstride) + (int64_t)(blockIdx.x % N) * N * N;
+    fft_slab_body<N, S, FastLayout<N>::SW>(in, out, twg, base, smem_raw);
+}
+
 // NP adjacent pencils (columns c, c+1) per thread.  grid.x = volumes * N (b)
 // * ceil(N / CPB) column blocks; pencils along the slowest axis.
+// Pencils along the slowest axis of the volume at `vbase` (complex values):
+// middle index b, column block cb; block of kFastThreads threads.
 template <int N, int S>
-__global__ void __launch_bounds__(kFastThreads)
-fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff) {
+__device__ __forceinline__ void fft_pencil_body(const float2* in, float2* out, const float2* __restrict__ twg,
+                                                int64_t vbase, int b, int cb, unsigned char* smem_raw) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, NP = L::NP, CPB = L::CPB;
-    constexpr int CBLK = (N + CPB - 1) / CPB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* exall = reinterpret_cast<float2*>(smem_raw);
     float2* tw = exall + kFastWarps * L::EXW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
     __syncthreads();
-    const int64_t blk = blockIdx.x;
-    const int64_t vol = blk / ((int64_t)N * CBLK);
-    const int rem = (int)(blk - vol * N * CBLK);
-    const int b = rem / CBLK;
-    const int cb = rem % CBLK;
     const int cl = lane % PPW, j = lane / PPW;
     if (cb * CPB + NP * warp * PPW >= N) return;   // warp-uniform; no block barrier below
     const int c = cb * CPB + NP * (warp * PPW + cl);
     const bool act = c < N;
     float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     const int64_t NN = (int64_t)N * N;
-    const int64_t base = vol_base(voff, vol, vstride) + (int64_t)b * N + c;
+    const int64_t base = vbase + (int64_t)b * N + c;
     float ar[R1], ai[R1], br[R1], bi[R1];
 #pragma unroll
     for (int m = 0; m < R1; ++m) {
@@ -296,6 +305,18 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg,
             }
         }
     }
+}
+
+template <int N, int S>
+__global__ void __launch_bounds__(kFastThreads)
+fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff) {
+    using L = FastLayout<N>;
+    constexpr int CBLK = (N + L::CPB - 1) / L::CPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t blk = blockIdx.x;
+    const int64_t vol = blk / ((int64_t)N * CBLK);
+    const int rem = (int)(blk - vol * N * CBLK);
+    fft_pencil_body<N, S>(in, out, twg, vol_base(voff, vol, vstride), rem / CBLK, rem % CBLK, smem_raw);
 }
 
 // Last pass of the forward transform of paired real volumes, fused with the

@@ -11,8 +11,8 @@
 
 namespace fcc {
 
-__constant__ int c_W[24][9];  // group matrices, row-major
-__constant__ int c_u[24][3];  // W_g^T (1,0,3)
+static __constant__ int c_W[24][9];  // group matrices, row-major
+static __constant__ int c_u[24][3];  // W_g^T (1,0,3)
 
 template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };

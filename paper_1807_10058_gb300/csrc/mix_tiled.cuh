@@ -21,7 +21,7 @@
 
 namespace fcc {
 
-__constant__ float2 c_core[3][24][24];  // free-orbit cores: forward, inverse, adjoint
+static __constant__ float2 c_core[3][24][24];  // free-orbit cores: forward, inverse, adjoint
 
 constexpr int kMaxClasses = 16;
 
@@ -126,21 +126,20 @@ __device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
 // of real volumes when PAIR: forward reads x1 + i x2 from volumes 2p, 2p+1
 // and writes Z to volume 2p of the complex output; inverse / adjoint read a
 // compact complex volume p and write Re / Im to real volumes 2p, 2p+1).
+// One warp's tile `tile` of volume `vol` (warp = threadIdx.x / 32 < kMixWarps
+// selects its shared-memory slot); a warp past ntiles returns at once.
 template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
-__global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
-                                                                   float* __restrict__ out, const TiledMixArgs a,
-                                                                   int ntiles, int tile0 = 0, int core_in_smem = 0,
-                                                                   const int64_t* voff = nullptr) {
+__device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, float* __restrict__ out,
+                                               const TiledMixArgs& a, int ntiles, int tile, int64_t vol,
+                                               int core_in_smem, const int64_t* voff, unsigned char* smem_raw) {
     constexpr bool CIN = (MODE != MODE_FWD) || !RIN || PAIR;    // complex values in the core
     constexpr bool COUT = (MODE == MODE_FWD) || !ROUT || PAIR;  // complex values out of the core
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
-    const int tile = tile0 + blockIdx.x * kMixWarps + warp;
     if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
     // unpaired volume offset (values): ragged batches pass a table of point offsets
-    const int64_t base = voff ? voff[blockIdx.y] : (int64_t)blockIdx.y * a.n3;
-    const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;  // paired: first volume of the pair
+    const int64_t base = voff ? voff[vol] : vol * a.n3;
+    const int64_t pb = vol * 2 * a.n3;  // paired: first volume of the pair
     const int o0 = a.tile_off[tile];
     const int cnt = a.tile_off[tile + 1] - o0;
     const int M8 = 8 * a.n;
@@ -305,6 +304,16 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
             }
         }
     });
+}
+
+template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
+__global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* __restrict__ in,
+                                                                   float* __restrict__ out, const TiledMixArgs a,
+                                                                   int ntiles, int tile0 = 0, int core_in_smem = 0,
+                                                                   const int64_t* voff = nullptr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    mix_tiled_body<MODE, RIN, ROUT, PAIR>(in, out, a, ntiles, tile0 + blockIdx.x * kMixWarps + (threadIdx.x >> 5),
+                                          blockIdx.y, core_in_smem, voff, smem_raw);
 }
 
 inline size_t mix_tiled_smem(int) { return (size_t)kMixWarps * 32 * kMixRow * 4; }

@@ -61,3 +61,10 @@ def test_describe_rejects_bad_order():
     n = ctypes.c_int64()
     assert L.fcc_dct_describe(0, ctypes.byref(n), None, None, None, None, None, None, None, None, None) \
         == binding.FCC_ERR_INVALID_ARG
+
+
+def test_schedule_calls_reject_null_plan():
+    L = binding.lib()
+    assert L.fcc_dct_set_schedule(None, 0, 32) == binding.FCC_ERR_INVALID_ARG
+    assert L.fcc_dct_get_schedule(None, 0) == -1
+    assert L.fcc_dct_autotune(None, None, None, None, 3, None) == binding.FCC_ERR_INVALID_ARG

@@ -1,0 +1,145 @@
+"""Execution schedules on the GPU: the persistent ragged launch, the schedule
+knobs and the autotuner change how the work runs, never what it computes.
+Results are compared with the oracle (or, across schedules, with each other
+to FP32 rounding), through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_10058_gb300 import binding, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _ragged(orders, seed, complex_in=False):
+    vols = [inputs.smoothed_noise(n, 1, seed=seed + i)[0] for i, n in enumerate(orders)]
+    flat = np.concatenate([v.reshape(-1) for v in vols])
+    if complex_in:
+        flat = flat + 1j * np.roll(flat, 11)
+    return flat
+
+
+def _check_against_oracle(y, flat, orders, tol):
+    off = 0
+    for i, n in enumerate(orders):
+        v = flat[off:off + n ** 3].reshape(n, n, n)
+        ref = oracle.forward_sum_fft(v.astype(np.complex128 if np.iscomplexobj(v) else np.float64), n).reshape(-1)
+        assert rel(y[off:off + n ** 3], ref) < tol, (i, n)
+        off += n ** 3
+
+
+@pytest.mark.parametrize("dtype", ["r32", "c32"])
+def test_persistent_ragged_launch_matches_oracle(dtype):
+    orders = inputs.ragged_orders(24, seed=9)
+    flat = _ragged(orders, seed=300, complex_in=dtype == "c32")
+    x = torch.from_numpy(flat.astype(np.float32 if dtype == "r32" else np.complex64)).to(DEV)
+    with binding.Plan(orders=orders, dtype=dtype) as p:
+        p.set_schedule(ragged=1)
+        assert p.schedule()["ragged"] == 1
+        assert p.launches(0) == 1
+        p.profile(True)
+        y = p.forward(x)
+        torch.cuda.synchronize()
+        rec = p.profile_read()
+        p.profile(False)
+        assert set(rec) == {"ragged_persistent"} and rec["ragged_persistent"][1] == 1
+        y = y.cpu().numpy()
+        p.set_schedule(ragged=0)
+        y0 = p.forward(x).cpu().numpy()
+    _check_against_oracle(y, flat, orders, 1e-5)
+    assert rel(y, y0) < 1e-6
+
+
+def test_persistent_ragged_launch_in_cuda_graph():
+    orders = [96, 8, 40, 64, 16, 88, 24]
+    flat = _ragged(orders, seed=17)
+    with binding.Plan(orders=orders, dtype="r32") as p:
+        p.set_schedule(ragged=1)
+        x = torch.from_numpy(flat.astype(np.float32)).to(DEV)
+        y = torch.empty(p.points, dtype=torch.complex64, device=DEV)
+        p.forward(x, out=y)            # outside the capture: kernel attributes
+        ref = y.clone()
+        y.zero_()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.forward(x, out=y)
+        torch.cuda.current_stream().wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
+
+
+def test_schedule_arguments_are_checked():
+    with binding.Plan(32, 2, "r32") as p:
+        L = binding.lib()
+        for key, bad in ((0, 0), (0, 2000), (1, 0), (1, 5), (2, 3), (3, 5), (9, 1)):
+            assert L.fcc_dct_set_schedule(p.handle, key, bad) == binding.FCC_ERR_INVALID_ARG
+        # one persistent launch is for ragged plans only
+        assert L.fcc_dct_set_schedule(p.handle, 2, 1) == binding.FCC_ERR_UNSUPPORTED
+        assert L.fcc_dct_get_schedule(p.handle, 9) == -1
+        assert p.schedule() == {"chunk_mb": 32, "streams": 2, "ragged": 0, "tc_blocks": 0}
+
+
+@pytest.mark.parametrize("dtype", ["r32", "r32_bf16x3"])
+def test_schedules_agree_on_uniform_batches(dtype):
+    n, batch = 64, 10
+    x = torch.from_numpy(inputs.phantom(n, batch, seed=5).astype(np.float32)).to(DEV)
+    with binding.Plan(n, batch, dtype) as p:
+        y0 = p.forward(x).cpu().numpy()
+        for sched in ({"chunk_mb": 4, "streams": 1}, {"chunk_mb": 64, "streams": 3}, {"streams": 4, "tc_blocks": 1}):
+            p.set_schedule(**sched)
+            y = p.forward(x).cpu().numpy()
+            assert rel(y, y0) < 1e-6, sched
+        # inverse and adjoint keep within the workspace sized at plan creation
+        back = p.inverse(p.forward(x)).cpu().numpy()
+        assert rel(back, x.cpu().numpy().reshape(-1)) < 1e-5
+
+
+@pytest.mark.parametrize("ragged", [False, True])
+def test_autotune_keeps_a_valid_schedule(ragged):
+    if ragged:
+        orders = inputs.ragged_orders(16, seed=21)
+        p = binding.Plan(orders=orders, dtype="r32")
+        flat = _ragged(orders, seed=50)
+    else:
+        p = binding.Plan(48, 8, "r32_bf16x3")
+        flat = inputs.phantom(48, 8, seed=6).reshape(-1)
+    with p:
+        x = torch.from_numpy(flat.astype(np.float32)).to(DEV)
+        y0 = p.forward(x).cpu().numpy()
+        out = torch.empty(p.points, dtype=torch.complex64, device=DEV)
+        ms, sched = p.autotune(x, out, reps=2)
+        assert ms > 0
+        assert 1 <= sched["streams"] <= 4 and sched["chunk_mb"] >= 1 and sched["ragged"] in (0, 1, 2)
+        y = p.forward(x).cpu().numpy()
+        assert rel(y, y0) < 1e-6
+
+
+@pytest.mark.parametrize("case", ["r32_n128", "bf16_n64", "ragged", "ragged_persistent", "inverse", "odd_n", "odd_n_inverse"])
+def test_launch_count_matches_recorded_launches(case):
+    if case.startswith("ragged"):
+        orders = inputs.ragged_orders(12, seed=2)
+        p = binding.Plan(orders=orders, dtype="r32")
+        if case == "ragged_persistent":
+            p.set_schedule(ragged=1)
+    else:
+        n, batch, dtype = {"r32_n128": (128, 5, "r32"), "bf16_n64": (64, 9, "r32_bf16x3"), "inverse": (64, 6, "r32"),
+                           "odd_n": (27, 5, "r32"), "odd_n_inverse": (27, 5, "r32")}[case]
+        p = binding.Plan(n, batch, dtype)
+    with p:
+        which = 1 if case.endswith("inverse") else 0
+        x = torch.zeros(p.points, dtype=torch.float32 if which == 0 else torch.complex64, device=DEV)
+        p.profile(True)
+        (p.forward if which == 0 else p.inverse)(x)
+        torch.cuda.synchronize()
+        rec = p.profile_read()
+        p.profile(False)
+        assert sum(c for _, c in rec.values()) == p.launches(which), rec
