@@ -63,6 +63,12 @@ struct OrderTables {
     // the free tiles' representatives padded to 32 per tile (0xffffffff = none)
     void* tc_core_image = nullptr;
     uint32_t* tc_reps32 = nullptr;
+    // ... and the boundary tiles: per-class core images, wrap offsets, and
+    // groups of up to 4 tiles of one class (see TcBoundary)
+    void* tc_core_images = nullptr;
+    int* tc_off = nullptr;
+    int* tc_bgroups = nullptr;
+    int tc_nbgroups = 0;
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
@@ -192,10 +198,33 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
                                                    : build_tc_core_image<1>(hp.classes[hp.free_class].fwd.data(), img);
         if (!ok) return FCC_ERR_UNSUPPORTED;
         if ((s = upload(p, &t.tc_core_image, img.data(), img.size()))) return s;
-        std::vector<uint32_t> r32((size_t)std::max(1, hp.free_tiles) * 32, 0xffffffffu);
-        for (int tl = 0; tl < hp.free_tiles; ++tl)
+        const int ntl = (int)hp.tile_off.size() - 1;
+        std::vector<uint32_t> r32((size_t)std::max(1, ntl) * 32, 0xffffffffu);
+        for (int tl = 0; tl < ntl; ++tl)
             for (int o = hp.tile_off[tl]; o < hp.tile_off[tl + 1]; ++o) r32[(size_t)tl * 32 + (o - hp.tile_off[tl])] = hp.tile_reps[o];
         if ((s = upload(p, (void**)&t.tc_reps32, r32.data(), r32.size() * 4))) return s;
+        // boundary classes: core images, wrap offsets, groups of <= 4 tiles
+        std::vector<unsigned char> imgs, one;
+        std::vector<int> off(hp.classes.size() * 24);
+        for (size_t c = 0; c < hp.classes.size(); ++c) {
+            const bool okc = p->dtype == FCC_R32_BF16X3 ? build_tc_core_image<0>(hp.classes[c].fwd.data(), one)
+                                                        : build_tc_core_image<1>(hp.classes[c].fwd.data(), one);
+            if (!okc) return FCC_ERR_UNSUPPORTED;
+            imgs.insert(imgs.end(), one.begin(), one.end());
+            for (int g = 0; g < 24; ++g)
+                off[c * 24 + g] = -n * (hp.classes[c].wrap[g][0] * n * n + hp.classes[c].wrap[g][1] * n + hp.classes[c].wrap[g][2]);
+        }
+        std::vector<int> groups;
+        for (int tl = hp.free_tiles; tl < ntl;) {
+            const int c = hp.tile_cls[hp.tile_off[tl]];
+            int grp[8] = {c, -1, -1, -1, -1, 0, 0, 0};
+            for (int w = 0; w < 4 && tl < ntl && hp.tile_cls[hp.tile_off[tl]] == c; ++w, ++tl) grp[1 + w] = tl;
+            groups.insert(groups.end(), grp, grp + 8);
+        }
+        t.tc_nbgroups = (int)(groups.size() / 8);
+        if ((s = upload(p, &t.tc_core_images, imgs.data(), imgs.size()))) return s;
+        if ((s = upload(p, (void**)&t.tc_off, off.data(), off.size() * 4))) return s;
+        if (!groups.empty() && (s = upload(p, (void**)&t.tc_bgroups, groups.data(), groups.size() * 4))) return s;
     }
     if ((s = upload(p, (void**)&t.tile_off, hp.tile_off.data(), hp.tile_off.size() * 4))) return s;
     if ((s = upload(p, (void**)&t.tile_reps, hp.tile_reps.data(), hp.tile_reps.size() * 4))) return s;
@@ -642,7 +671,8 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
         const float* src = in + v0 * a.n3 * 2;
         float* dst = out + v0 * a.n3 * 4;
         if (t.free_tiles > 0 && t.tc_core_image) {
-            const int ngroups = (t.free_tiles + 3) / 4;
+            const int ngroups = (t.free_tiles + 3) / 4 + t.tc_nbgroups;
+            const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups, (const uint4*)t.tc_core_images, t.tc_off, t.canon_mask};
             const int lim = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
             const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, lim) : lim;
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
@@ -650,10 +680,10 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             ProfScope ps("mix_tc_fwd", st);
             if (bf16)
                 mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status);
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd);
             else
                 mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status);
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd);
         }
         if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
@@ -691,7 +721,9 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     // forward: the boundary (non-free) tiles of every pair in one launch on a
     // stream of their own, concurrent with the chunks' free mixing; each
     // chunk's DFT passes wait for it
-    const bool split_boundary = which == 0 && npairs > 0 && t.free_tiles > 0 && t.ntiles > t.free_tiles;
+    // (the tensor-core kernel takes the boundary tiles itself)
+    const bool tc_all = is_tc(p->dtype) && t.tc_core_image;
+    const bool split_boundary = which == 0 && npairs > 0 && t.free_tiles > 0 && t.ntiles > t.free_tiles && !tc_all;
     if (split_boundary) {
         if (cudaStreamWaitEvent(p->bnd_stream, p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
         s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, npairs, 1.f, p->bnd_stream, true, 2);
@@ -704,10 +736,8 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             const float* x = in + 2 * p0 * n3;
             float* y = out + 2 * p0 * n3 * 2;
             const int part = split_boundary ? 1 : 0;
-            if (is_tc(p->dtype) && t.tc_core_image) {
+            if (tc_all) {
                 s = launch_mix_tc_pairs(p, t, x, y, np, ss);
-                if (!s && !split_boundary && t.ntiles > t.free_tiles)
-                    s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, 2);
             } else if (is_tc(p->dtype)) {
                 s = launch_mix_tc_pairs(p, t, x, y, np, ss);
             } else {
@@ -1092,17 +1122,18 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
             const OrderTables& tb = p->tabs.at(n);
             const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
             const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
+            const bool tc_all = is_tc(p->dtype) && tb.tc_core_image;   // one launch mixes every tile
             const int64_t npairs = pairing ? nv / 2 : 0;
             // per paired chunk: mixing, then the DFT passes and the pair split /
             // merge (the fast forward fuses the split into its pencil pass;
             // generic passes over strided pairs go pair by pair)
-            const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
+            const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles && !tc_all;
             if (split_b) total += 1;
             for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
                 const int64_t np = std::min(cv, npairs - p0);
                 // (the inverse / adjoint merge into a compact workspace first)
                 const int64_t dft_pair = has_fast_fft(n) ? (which == 0 ? 2 : 3) : (which == 0 ? 3 * np + 1 : 4);
-                total += (int)((split_b ? 1 : mixl) + dft_pair);
+                total += (int)((split_b || (tc_all && which == 0) ? 1 : mixl) + dft_pair);
             }
             const int64_t rest = nv - 2 * npairs;
             total += (int)(((rest + cv - 1) / cv) * (mixl + dft));

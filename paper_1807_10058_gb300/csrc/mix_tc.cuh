@@ -126,13 +126,16 @@ __device__ __forceinline__ void store_half(unsigned char* X, int row, const floa
 }
 
 // Loads of slots H .. H + 11 of representative rp (both volumes of the pair).
+// off: per-slot wrap offsets of a boundary class (nullptr: the free class's,
+// a.lin[g][3]).
 template <int H>
 __device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* in0, const float* in1, uint32_t rp,
-                                            float* vr, float* vi) {
+                                            const int* off, float* vr, float* vi) {
     const bool act = rp != 0xffffffffu;
     static_for<0, 12>([&](auto Sc) {
         constexpr int g = H + decltype(Sc)::value;
-        const int gi = act ? rep_dot(rp, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3] : 0;
+        const int o = off ? __ldg(off + g) : a.lin[g][3];
+        const int gi = act ? rep_dot(rp, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + o : 0;
         vr[g - H] = act ? __ldg(in0 + gi) : 0.f;
         vi[g - H] = act ? __ldg(in1 + gi) : 0.f;
     });
@@ -140,9 +143,11 @@ __device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* 
 
 // Epilogue for slots H .. H + 11 of this thread's orbit: TMEM columns 4H ..
 // 4H + 47 of lane trow, A1 + A2 / sqrt 2, row phase R_g / 24, scatter.
+// off, cmask: wrap offsets and canonical slots of the tile's class (a
+// boundary class writes each of its distinct points once).
 template <int H>
-__device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t trow, uint32_t rep, float2* out,
-                                              int64_t pb, int M8) {
+__device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t trow, uint32_t rep, const int* off,
+                                              uint32_t cmask, float2* out, int64_t pb, int M8) {
     const float rs2 = 0.70710678118654752440f;
     const float sc = 1.0f / 24.0f;
 #pragma unroll
@@ -162,21 +167,37 @@ __device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t tr
                 const float im = fmaf(__uint_as_float(v[4 * s4 + 3]), rs2, __uint_as_float(v[4 * s4 + 1]));
                 int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
                 q = q < 0 ? q + M8 : q;
-                const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + a.lin[g][3];
-                const float2 R = __ldg(a.phase + q);
-                out[pb + gi] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
+                const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + (off ? __ldg(off + g) : a.lin[g][3]);
+                if ((cmask >> g) & 1u) {
+                    const float2 R = __ldg(a.phase + q);
+                    out[pb + gi] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
+                }
             });
         }
     }
 }
 
-// grid.x: blocks looping over groups of 4 free tiles; grid.y: pairs of real volumes.
-// reps32: representatives of the free tiles, 32 per tile, 0xffffffff = none.
+// Boundary (non-free) tiles on the tensor cores: groups of up to 4 tiles of
+// one class, after the free groups.  group[8 g] = class, group[8 g + 1 + w] =
+// tile of warp w (-1: none); per class: its core image (the free core's
+// layout), wrap offsets off[24 c + g] and canonical-slot mask.
+struct TcBoundary {
+    const int* group;
+    int ngroups;
+    const uint4* core_images;   // [class][core_bytes / 16]
+    const int* off;
+    const uint32_t* canon_mask;
+};
+
+// grid.x: blocks looping over groups of 4 free tiles, then the boundary
+// groups; grid.y: pairs of real volumes.
+// reps32: representatives of every tile, 32 per tile, 0xffffffff = none.
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
-                       const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status) {
+                       const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status,
+                       const TcBoundary bnd) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* Cs = smem_raw;                 // core, 96 x 48
@@ -213,28 +234,47 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     const uint32_t kNone = 0xffffffffu;
     const float* __restrict__ in0 = in + pb;
     const float* __restrict__ in1 = in + pb + a.n3;
+    const int nall = ngroups + bnd.ngroups;
+    // class of group g (block-uniform; free class for the free groups)
+    auto cls_of = [&](int g) -> int { return g < ngroups || g >= nall ? a.free_class : __ldg(bnd.group + 8 * (g - ngroups)); };
     auto rep_of = [&](int g) -> uint32_t {
-        const int tile = g * 4 + wq;
-        return (g < ngroups && tile < nfree_tiles) ? __ldg(reps32 + (size_t)tile * 32 + lane) : kNone;
+        if (g < ngroups) {
+            const int tile = g * 4 + wq;
+            return tile < nfree_tiles ? __ldg(reps32 + (size_t)tile * 32 + lane) : kNone;
+        }
+        if (g >= nall) return kNone;
+        const int tile = __ldg(bnd.group + 8 * (g - ngroups) + 1 + wq);
+        return tile >= 0 ? __ldg(reps32 + (size_t)tile * 32 + lane) : kNone;
     };
     float vr[12], vi[12];
-    auto gather = [&](uint32_t rp) {   // warp-uniform branch on the slot half
-        if (half == 0) gather_half<0>(a, in0, in1, rp, vr, vi);
-        else gather_half<12>(a, in0, in1, rp, vr, vi);
+    auto gather = [&](uint32_t rp, int c) {   // warp-uniform branch on the slot half
+        const int* off = c == a.free_class ? nullptr : bnd.off + 24 * c;
+        if (half == 0) gather_half<0>(a, in0, in1, rp, off, vr, vi);
+        else gather_half<12>(a, in0, in1, rp, off, vr, vi);
     };
 
     const int gstep = (int)gridDim.x;
     int grp = blockIdx.x;
+    int core_cls = a.free_class;   // class whose core image is in Cs
     uint32_t rcur = rep_of(grp), rnext = rep_of(grp + gstep);
-    if (grp < ngroups) gather(rcur);
-    for (; grp < ngroups && ok; grp += gstep) {
+    int ccur = cls_of(grp), cnext = cls_of(grp + gstep);
+    if (grp < nall) gather(rcur, ccur);
+    for (; grp < nall && ok; grp += gstep) {
         const uint32_t rep = rcur;
+        const int cls = ccur;
+        if (cls != core_cls) {   // block-uniform; the previous MMA has completed
+            const uint4* src = bnd.core_images + (size_t)cls * (L::core_bytes / 16);
+            for (int e = tid; e < (int)(L::core_bytes / 16); e += kTcThreads) reinterpret_cast<uint4*>(Cs)[e] = __ldg(src + e);
+            core_cls = cls;
+        }
         if (half == 0) store_half<KIND, 0>(Xs, row, vr, vi);
         else store_half<KIND, 12>(Xs, row, vr, vi);
         // the next tile's loads overlap the barrier, the MMAs, the wait and the epilogue
         rcur = rnext;
-        if (grp + gstep < ngroups) gather(rcur);
+        ccur = cnext;
+        if (grp + gstep < nall) gather(rcur, ccur);
         rnext = rep_of(grp + 2 * gstep);
+        cnext = cls_of(grp + 2 * gstep);
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -273,8 +313,10 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {   // warp-uniform: tcgen05.ld is executed by whole warps
-            if (half == 0) epilogue_half<0>(a, trow, rep, reinterpret_cast<float2*>(out), pb, M8);
-            else epilogue_half<12>(a, trow, rep, reinterpret_cast<float2*>(out), pb, M8);
+            const int* off = cls == a.free_class ? nullptr : bnd.off + 24 * cls;
+            const uint32_t cm = cls == a.free_class ? 0xffffffu : __ldg(bnd.canon_mask + cls);
+            if (half == 0) epilogue_half<0>(a, trow, rep, off, cm, reinterpret_cast<float2*>(out), pb, M8);
+            else epilogue_half<12>(a, trow, rep, off, cm, reinterpret_cast<float2*>(out), pb, M8);
         }
         // TMEM reads complete before the next tile's MMAs (issued after the next barrier)
         asm volatile("tcgen05.fence::before_thread_sync;");
