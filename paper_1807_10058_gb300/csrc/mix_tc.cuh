@@ -299,11 +299,16 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar)));
         }
-        uint32_t done = 0;
-        for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
-            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done)
-                         : "r"(smem_addr(bar)), "r"(phase));
+        // thread 0 waits for the MMAs; the block barrier below passes the
+        // completion on to the other threads
+        uint32_t done = 1;
+        if (tid == 0) {
+            done = 0;
+            for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
+                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                             : "=r"(done)
+                             : "r"(smem_addr(bar)), "r"(phase));
+            }
         }
         phase ^= 1u;
         // block-uniform decision: every thread must take the same path below
