@@ -368,13 +368,17 @@ def main():
     ck = clocks.stop()
     ms = slowest_rank_ms(ms, dist, dev)
 
-    # per-kernel durations: the same K steps again with per-launch events
+    # per-kernel durations: the same K steps again with per-launch events on
+    # one internal stream, so that each kernel is timed alone
+    sched = plan.schedule()
+    plan.set_schedule(streams=1)
     plan.profile(True)
     for _ in range(args.steps):
         plan.forward(x, out=y)
     torch.cuda.synchronize()
     kern = plan.profile_read()
     plan.profile(False)
+    plan.set_schedule(streams=sched["streams"])
     # algorithmic bytes per real point of each kernel.  Real plans pair two
     # volumes per complex transform: the mixing reads x (4 B) and writes half a
     # complex value (4 B); each DFT pass reads and writes half a complex value;
@@ -460,6 +464,11 @@ def main():
                          "algorithmic_bytes_per_point": algo_bytes.get(top_name, 12)},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": 12},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+            "kernels": {k: {"launches_per_step": v[1] / args.steps, "ms_per_launch": v[0] / v[1],
+                            "achieved_gbs": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9,
+                            "frac": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9 / peak}
+                        for k, v in kern.items()},
+            "kernel_timing": "CUDA events around each launch, one internal stream (each kernel alone)",
             "e2e": {"value": world * pts / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 8)},
             "gpu_launches": plan.launches(0) * args.steps,

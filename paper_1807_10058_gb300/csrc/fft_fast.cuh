@@ -120,6 +120,55 @@ struct PencilFft {
             for (int k1 = 0; k1 < G; ++k1) emit(q + G * e + R1 * k1, ur[e][k1], ui[e][k1]);
         }
     }
+
+    // two independent pencils in lockstep (more independent work per warp);
+    // they share the exchange slot one after the other.  emit(p, index, re, im)
+    template <typename Emit>
+    __device__ __forceinline__ static void run2(float (&ar)[R1], float (&ai)[R1], float (&br)[R1], float (&bi)[R1],
+                                                int j, float2* ex, const float2* tw, Emit emit) {
+        constexpr int E = R1 / G;
+        reg::Dft<R1, S, float>::run(ar, ai);
+        reg::Dft<R1, S, float>::run(br, bi);
+#pragma unroll
+        for (int k2 = 1; k2 < R1; ++k2) {
+            const float2 w = tw[(j * k2) % N];
+            const float wi = S > 0 ? w.y : -w.y;
+            float t = ar[k2] * w.x - ai[k2] * wi;
+            ai[k2] = ar[k2] * wi + ai[k2] * w.x;
+            ar[k2] = t;
+            t = br[k2] * w.x - bi[k2] * wi;
+            bi[k2] = br[k2] * wi + bi[k2] * w.x;
+            br[k2] = t;
+        }
+        float ur[2][E][G], ui[2][E][G];
+#pragma unroll
+        for (int pz = 0; pz < 2; ++pz) {
+#pragma unroll
+            for (int k2 = 0; k2 < R1; ++k2)
+                ex[j * (R1 + 1) + k2] = pz ? make_float2(br[k2], bi[k2]) : make_float2(ar[k2], ai[k2]);
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+#pragma unroll
+                for (int jj = 0; jj < G; ++jj) {
+                    const float2 t = ex[jj * (R1 + 1) + j + G * e];
+                    ur[pz][e][jj] = t.x;
+                    ui[pz][e][jj] = t.y;
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            reg::Dft<G, S, float>::run(ur[0][e], ui[0][e]);
+            reg::Dft<G, S, float>::run(ur[1][e], ui[1][e]);
+#pragma unroll
+            for (int k1 = 0; k1 < G; ++k1) {
+                emit(0, j + G * e + R1 * k1, ur[0][e][k1], ui[0][e][k1]);
+                emit(1, j + G * e + R1 * k1, ur[1][e][k1], ui[1][e][k1]);
+            }
+        }
+    }
 };
 
 __device__ __forceinline__ int64_t vol_base(const int64_t* voff, int64_t v, int64_t vstride) {
@@ -167,8 +216,20 @@ __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, con
                     vi[rd][m] = t.y;
                 }
             }
+            // two rounds in lockstep where every row of both exists
+            constexpr int NP2 = N % RR == 0 ? NR / 2 * 2 : 0;
 #pragma unroll
-            for (int rd = 0; rd < NR; ++rd) {
+            for (int rd = 0; rd < NP2; rd += 2) {
+                const int r0 = rd * RR + warp * PPW + p, r1 = r0 + RR;
+                float2* row0 = slab + r0 * LD;
+                float2* row1 = slab + r1 * LD;
+                PencilFft<N, S>::run2(vr[rd], vi[rd], vr[rd + 1], vi[rd + 1], j, ex, tw,
+                                      [&](int pz, int c, float xr, float xi) {
+                                          (pz ? row1 : row0)[c] = make_float2(xr, xi);
+                                      });
+            }
+#pragma unroll
+            for (int rd = NP2; rd < NR; ++rd) {
                 if (rd * RR + warp * PPW >= N) continue;   // warp-uniform
                 const int r = rd * RR + warp * PPW + p;
                 const bool act = r < N;
@@ -202,21 +263,43 @@ __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, con
     {
         const int cl = lane % PPW, j = lane / PPW;
         float2* ex = exall + warp * L::EXW + cl * L::EXPC;
-        for (int c0 = 0; c0 < N; c0 += SW * PPW) {
-            if (c0 + warp * PPW >= N) continue;   // warp-uniform
-            const int c = c0 + warp * PPW + cl;
-            const bool act = c < N;
-            float vr[R1], vi[R1];
+        constexpr int CR = SW * PPW;   // columns per round
+        if (N % (2 * CR) == 0 && R1 <= 16) {
+            // two column rounds in lockstep (every column exists)
+            for (int c0 = 0; c0 < N; c0 += 2 * CR) {
+                const int c = c0 + warp * PPW + cl;
+                float ar[R1], ai[R1], br[R1], bi[R1];
 #pragma unroll
-            for (int m = 0; m < R1; ++m) {
-                const float2 t = act ? slab[(j + G * m) * LD + c] : make_float2(0.f, 0.f);
-                vr[m] = t.x;
-                vi[m] = t.y;
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = slab[(j + G * m) * LD + c];
+                    const float2 u = slab[(j + G * m) * LD + c + CR];
+                    ar[m] = t.x;
+                    ai[m] = t.y;
+                    br[m] = u.x;
+                    bi[m] = u.y;
+                }
+                float2* dst = out + base + c;
+                PencilFft<N, S>::run2(ar, ai, br, bi, j, ex, tw, [&](int pz, int b, float xr, float xi) {
+                    dst[(int64_t)b * N + (pz ? CR : 0)] = make_float2(xr, xi);
+                });
             }
-            float2* dst = out + base + c;
-            PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int b, float xr, float xi) {
-                if (act) dst[(int64_t)b * N] = make_float2(xr, xi);
-            });
+        } else {
+            for (int c0 = 0; c0 < N; c0 += CR) {
+                if (c0 + warp * PPW >= N) continue;   // warp-uniform
+                const int c = c0 + warp * PPW + cl;
+                const bool act = c < N;
+                float vr[R1], vi[R1];
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    const float2 t = act ? slab[(j + G * m) * LD + c] : make_float2(0.f, 0.f);
+                    vr[m] = t.x;
+                    vi[m] = t.y;
+                }
+                float2* dst = out + base + c;
+                PencilFft<N, S>::run(vr, vi, j, ex, tw, [&](int b, float xr, float xi) {
+                    if (act) dst[(int64_t)b * N] = make_float2(xr, xi);
+                });
+            }
         }
     }
 }
