@@ -128,13 +128,13 @@ __device__ __forceinline__ void store_half(unsigned char* X, int row, const floa
 // Loads of slots H .. H + 11 of representative rp (both volumes of the pair).
 // off: per-slot wrap offsets of a boundary class (nullptr: the free class's,
 // a.lin[g][3]).
-template <int H>
+template <int H, bool BND>
 __device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* in0, const float* in1, uint32_t rp,
                                             const int* off, float* vr, float* vi) {
     const bool act = rp != 0xffffffffu;
     static_for<0, 12>([&](auto Sc) {
         constexpr int g = H + decltype(Sc)::value;
-        const int o = off ? __ldg(off + g) : a.lin[g][3];
+        const int o = BND ? __ldg(off + g) : a.lin[g][3];
         const int gi = act ? rep_dot(rp, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + o : 0;
         vr[g - H] = act ? __ldg(in0 + gi) : 0.f;
         vi[g - H] = act ? __ldg(in1 + gi) : 0.f;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* 
 // 4H + 47 of lane trow, A1 + A2 / sqrt 2, row phase R_g / 24, scatter.
 // off, cmask: wrap offsets and canonical slots of the tile's class (a
 // boundary class writes each of its distinct points once).
-template <int H>
+template <int H, bool BND>
 __device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t trow, uint32_t rep, const int* off,
                                               uint32_t cmask, float2* out, int64_t pb, int M8) {
     const float rs2 = 0.70710678118654752440f;
@@ -167,8 +167,8 @@ __device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t tr
                 const float im = fmaf(__uint_as_float(v[4 * s4 + 3]), rs2, __uint_as_float(v[4 * s4 + 1]));
                 int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
                 q = q < 0 ? q + M8 : q;
-                const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + (off ? __ldg(off + g) : a.lin[g][3]);
-                if ((cmask >> g) & 1u) {
+                const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + (BND ? __ldg(off + g) : a.lin[g][3]);
+                if (!BND || ((cmask >> g) & 1u)) {
                     const float2 R = __ldg(a.phase + q);
                     out[pb + gi] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
                 }
@@ -247,10 +247,15 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         return tile >= 0 ? __ldg(reps32 + (size_t)tile * 32 + lane) : kNone;
     };
     float vr[12], vi[12];
-    auto gather = [&](uint32_t rp, int c) {   // warp-uniform branch on the slot half
-        const int* off = c == a.free_class ? nullptr : bnd.off + 24 * c;
-        if (half == 0) gather_half<0>(a, in0, in1, rp, off, vr, vi);
-        else gather_half<12>(a, in0, in1, rp, off, vr, vi);
+    auto gather = [&](uint32_t rp, int c) {   // warp-uniform branches: slot half, free or boundary class
+        if (c == a.free_class) {
+            if (half == 0) gather_half<0, false>(a, in0, in1, rp, nullptr, vr, vi);
+            else gather_half<12, false>(a, in0, in1, rp, nullptr, vr, vi);
+        } else {
+            const int* off = bnd.off + 24 * c;
+            if (half == 0) gather_half<0, true>(a, in0, in1, rp, off, vr, vi);
+            else gather_half<12, true>(a, in0, in1, rp, off, vr, vi);
+        }
     };
 
     const int gstep = (int)gridDim.x;
@@ -318,10 +323,16 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {   // warp-uniform: tcgen05.ld is executed by whole warps
-            const int* off = cls == a.free_class ? nullptr : bnd.off + 24 * cls;
-            const uint32_t cm = cls == a.free_class ? 0xffffffu : __ldg(bnd.canon_mask + cls);
-            if (half == 0) epilogue_half<0>(a, trow, rep, off, cm, reinterpret_cast<float2*>(out), pb, M8);
-            else epilogue_half<12>(a, trow, rep, off, cm, reinterpret_cast<float2*>(out), pb, M8);
+            float2* o2 = reinterpret_cast<float2*>(out);
+            if (cls == a.free_class) {
+                if (half == 0) epilogue_half<0, false>(a, trow, rep, nullptr, 0u, o2, pb, M8);
+                else epilogue_half<12, false>(a, trow, rep, nullptr, 0u, o2, pb, M8);
+            } else {
+                const int* off = bnd.off + 24 * cls;
+                const uint32_t cm = __ldg(bnd.canon_mask + cls);
+                if (half == 0) epilogue_half<0, true>(a, trow, rep, off, cm, o2, pb, M8);
+                else epilogue_half<12, true>(a, trow, rep, off, cm, o2, pb, M8);
+            }
         }
         // TMEM reads complete before the next tile's MMAs (issued after the next barrier)
         asm volatile("tcgen05.fence::before_thread_sync;");
