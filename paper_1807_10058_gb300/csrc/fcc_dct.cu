@@ -652,6 +652,23 @@ fcc_status dft3_split_pairs(const OrderTables& t, float* y, int64_t np, cudaStre
     return s ? s : launch_pair(true, t.n, nullptr, y, np, st);
 }
 
+// Inverse / adjoint of `np` paired chunks: W = P(v1) + i P(v2) into the compact
+// workspace and its - sign 3-D DFT; the fast path fuses the merge into the
+// first (pencil) pass.
+fcc_status merge_dft3_pairs(const OrderTables& t, const float* y, float* ws, int64_t np, cudaStream_t st) {
+    if (has_fast_fft(t.n) && ((((uintptr_t)y) | ((uintptr_t)ws)) & 15u) == 0) {
+        const float2* tw = (const float2*)t.tw;
+        {
+            ProfScope ps("fft_pencil_merge", st);
+            if (launch_fast_pencil_merge(t.n, (const float2*)y, (float2*)ws, np, tw, st) != cudaSuccess) return FCC_ERR_CUDA;
+        }
+        const int64_t n3 = (int64_t)t.n * t.n * t.n;
+        return fast_fft(t.n, true, -1, (const float2*)ws, (float2*)ws, np, tw, n3, st);
+    }
+    fcc_status s = launch_pair(false, t.n, y, ws, np, st);
+    return s ? s : launch_dft3(t, -1, ws, ws, np, st);
+}
+
 // Forward mixing of `np` pairs of real volumes with the orbit core on the
 // tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
@@ -749,8 +766,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
             const float* y = in + 2 * p0 * n3 * 2;
             float* x = out + 2 * p0 * n3;
-            s = launch_pair(false, t.n, y, ws, np, ss);
-            if (!s) s = launch_dft3(t, -1, ws, ws, np, ss);
+            s = merge_dft3_pairs(t, y, ws, np, ss);
             const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
             if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, true, ws, x, np, scale, ss, true);
         }
@@ -1132,7 +1148,7 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
             for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
                 const int64_t np = std::min(cv, npairs - p0);
                 // (the inverse / adjoint merge into a compact workspace first)
-                const int64_t dft_pair = has_fast_fft(n) ? (which == 0 ? 2 : 3) : (which == 0 ? 3 * np + 1 : 4);
+                const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
                 total += (int)((split_b || (tc_all && which == 0) ? 1 : mixl) + dft_pair);
             }
             const int64_t rest = nv - 2 * npairs;

@@ -51,7 +51,34 @@ cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const f
     return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const float2* tw, cudaStream_t st) {
+    using L = FastLayout<N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(fft_pencil_merge_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        attr = true;
+    }
+    const int64_t n3 = (int64_t)N * N * N;
+    const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
+    if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+    fft_pencil_merge_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
+                                     cudaStream_t st) {
+    switch (n) {
+#define FCC_CASE(NN) case NN: return launch_merge_n<NN>(in, out, npairs, tw, st);
+        FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
+        FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
+#undef FCC_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
                                     int64_t vstride, cudaStream_t st) {

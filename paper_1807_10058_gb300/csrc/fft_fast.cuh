@@ -504,10 +504,99 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     }
 }
 
+// First pass of the inverse / adjoint of paired real volumes, fused with the
+// merge W = P(v1) + i P(v2), P(v)[a] = (v[a] + conj(v[pi(a)])) / 2 (see
+// pair.cuh): the same primary / partner pencils as fft_pencil_pair_kernel.
+// Each half of the block loads its pencil of v1 and v2 (volumes 2p, 2p + 1
+// at p * in_vstride), the raw pencils meet in shared memory (v1, then v2),
+// every thread forms W at its own pencil and transforms it along the slow
+// axis with the - sign, written to the compact volume p at p * out_vstride.
+// Row 0's partner warps idle; in row n/2 only columns q < n/2 are primary.
+template <int N>
+__global__ void __launch_bounds__(kFastThreads)
+fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ twg,
+                        int64_t in_vstride, int64_t out_vstride) {
+    using L = FastLayout<N>;
+    using P = PairLayout<N>;
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
+    constexpr int ROWS = N / 2 + 1;
+    constexpr int64_t NN = (int64_t)N * N, N3 = NN * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* exall = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = exall + kFastWarps * L::EXW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    const int64_t blk = blockIdx.x;
+    const int64_t pr = blk / (ROWS * P::CBLK);
+    const int rem = (int)(blk - pr * ROWS * P::CBLK);
+    const int l = rem / P::CBLK, cb = rem % P::CBLK;
+    const int qlim = 2 * l == N ? N / 2 : N;
+    const bool partner = warp >= kFastWarps / 2;
+    const int wq = partner ? warp - kFastWarps / 2 : warp;
+    const int cl = lane % PPW, j = lane / PPW;
+    const int c = cb * P::CPB2 + wq * PPW + cl;
+    const bool idle = cb * P::CPB2 + wq * PPW >= qlim || (partner && l == 0);   // warp-uniform
+    const bool act = !idle && c < qlim;
+    const int lo = partner ? (N - l) % N : l;
+    const int co = partner ? (c - l + N) % N : c;
+    const int64_t pin = pr * in_vstride + (int64_t)lo * N + co;     // + k * NN; v2 at + N3
+    const int64_t pout = pr * out_vstride + (int64_t)lo * N + co;
+    float2* ex = exall + warp * L::EXW + cl * L::EXPC;
+    const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXPC;
+    const int sh = partner ? l : N - l;   // counterpart index k + sh (mod N)
+    float v1r[R1], v1i[R1], v2r[R1], v2i[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+        const int64_t o = (int64_t)(j + G * m) * NN;
+        const float2 a = act ? in[pin + o] : make_float2(0.f, 0.f);
+        const float2 b = act ? in[pin + N3 + o] : make_float2(0.f, 0.f);
+        v1r[m] = a.x;
+        v1i[m] = a.y;
+        v2r[m] = b.x;
+        v2i[m] = b.y;
+    }
+    float wr[R1], wi[R1];
+#pragma unroll
+    for (int vv = 0; vv < 2; ++vv) {
+        const float* vr = vv ? v2r : v1r;
+        const float* vi = vv ? v2i : v1i;
+        if (!idle) {
+#pragma unroll
+            for (int m = 0; m < R1; ++m) ex[j + G * m] = make_float2(vr[m], vi[m]);
+        }
+        __syncthreads();
+        if (!idle) {
+#pragma unroll
+            for (int m = 0; m < R1; ++m) {
+                int kc = j + G * m + sh;
+                kc -= kc >= N ? N : 0;
+                const float2 B = cx[kc];
+                const float pr_ = 0.5f * (vr[m] + B.x), pi_ = 0.5f * (vi[m] - B.y);   // P(v) at this point
+                if (vv == 0) {
+                    wr[m] = pr_;
+                    wi[m] = pi_;
+                } else {   // W = P(v1) + i P(v2)
+                    wr[m] -= pi_;
+                    wi[m] += pr_;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (idle) return;   // no block barrier below
+    PencilFft<N, -1>::run(wr, wi, j, ex, tw, [&](int k, float xr, float xi) {
+        if (act) out[pout + (int64_t)k * NN] = make_float2(xr, xi);
+    });
+}
+
 // Host launchers (fft_fast.cu).
 bool has_fast_fft(int n);
 cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2* out, int64_t nvol,
                             const float2* tw, int64_t vstride, const int64_t* voff, cudaStream_t st);
+// inverse / adjoint: pair merge + first (pencil) pass, pairs at p * 2 n^3 of in,
+// compact results at p * n^3 of out
+cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
+                                     cudaStream_t st);
 // forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
                                     int64_t vstride, cudaStream_t st);
