@@ -172,6 +172,18 @@ fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, voi
 fcc_status fcc_dct_check(fcc_plan* plan);
 
 /*
+ * Test hook for the device-side failure detection (no counterpart in the
+ * paper).  With enable != 0 the tensor-core kernels of a tensor-core plan
+ * issue no MMA and no completion signal, so their bounded wait runs out after
+ * a short limit (65536 non-blocking polls): the kernel records the
+ * timeout, releases its tensor memory and returns without writing its
+ * output, and the next fcc_dct_check reports FCC_ERR_TIMEOUT.  The GPU is
+ * neither hung nor faulted; later calls with enable = 0 run normally.
+ * FCC_ERR_UNSUPPORTED for plans without a tensor-core form.
+ */
+fcc_status fcc_dct_test_wait_timeout(fcc_plan* plan, int enable);
+
+/*
  * Execution schedule.  The paper has no counterpart: these knobs change only
  * how the plan's work is laid out on the GPU (the results agree to FP32
  * rounding order).  Keys and values:

@@ -21,7 +21,7 @@ EXPORTS = [
     "fcc_dct_in_bytes", "fcc_dct_out_bytes", "fcc_dct_launches", "fcc_dct_last_error",
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
     "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
-    "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune",
+    "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune", "fcc_dct_test_wait_timeout",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -82,6 +82,8 @@ def lib():
         L.fcc_dct_get_schedule.restype = i32
         L.fcc_dct_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float)]
         L.fcc_dct_autotune.restype = i32
+        L.fcc_dct_test_wait_timeout.argtypes = [vp, i32]
+        L.fcc_dct_test_wait_timeout.restype = i32
         _LIB = L
     return _LIB
 

@@ -100,6 +100,7 @@ struct fcc_plan {
     bool ragged_fast = true;         // ragged FP32 forward: per-order launches over offset tables
     int ragged_mode = 0;             // FCC_SCHED_RAGGED: 0 per-order launches, 1 one persistent launch, 2 per run of volumes
     int tc_blocks = 0;               // FCC_SCHED_TC_BLOCKS: tensor-core mixing blocks per SM in the grid (0 = resident maximum)
+    int wait_test = 0;               // fcc_dct_test_wait_timeout
     int scratch_streams = 1;         // internal streams the inverse / adjoint workspace was sized for
     int num_sms = 1;
     int* d_status = nullptr;         // device-side wait timeouts (tensor-core kernels)
@@ -697,10 +698,10 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             ProfScope ps("mix_tc_fwd", st);
             if (bf16)
                 mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd);
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
             else
                 mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd);
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
         }
         if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
@@ -1197,6 +1198,13 @@ int fcc_dct_profile_read(fcc_plan* p, char* names, double* ms, int* launches, in
         if (launches) launches[k] = cnt[k];
     }
     return (int)kinds.size();
+}
+
+fcc_status fcc_dct_test_wait_timeout(fcc_plan* p, int enable) {
+    if (!p) return fail(FCC_ERR_INVALID_ARG);
+    if (!is_tc(p->dtype)) return fail(FCC_ERR_UNSUPPORTED);
+    p->wait_test = enable != 0;
+    return FCC_OK;
 }
 
 fcc_status fcc_dct_check(fcc_plan* p) {

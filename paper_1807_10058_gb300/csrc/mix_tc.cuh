@@ -45,6 +45,7 @@ namespace fcc {
 constexpr int kTcThreads = 256;   // two threads per orbit: slots 0-11 and 12-23
 constexpr int kTcK = 48;                       // real inputs per orbit
 constexpr uint32_t kTcWaitLimit = 1u << 26;    // bounded mbarrier wait
+constexpr uint32_t kTcTestWaitLimit = 1u << 16;   // non-blocking polls of the timeout test
 
 template <int KIND>  // 0: BF16 terms, 1: TF32 terms
 struct TcLayout {
@@ -193,11 +194,13 @@ struct TcBoundary {
 // groups; grid.y: pairs of real volumes.
 // reps32: representatives of every tile, 32 per tile, 0xffffffff = none.
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
+// wait_test: issue no MMA and no completion signal, so that the (shortened)
+// wait runs out -- the test of the timeout path; nothing is written then.
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
                        const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status,
-                       const TcBoundary bnd) {
+                       const TcBoundary bnd, int wait_test) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* Cs = smem_raw;                 // core, 96 x 48
@@ -284,7 +287,7 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
+        if (tid == 0 && !wait_test) {
             const uint32_t xb = smem_addr(Xs), cb = smem_addr(Cs);
 #pragma unroll
             for (int t = 0; t < L::TERMS; ++t) {
@@ -309,10 +312,18 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         uint32_t done = 1;
         if (tid == 0) {
             done = 0;
-            for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
-                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                             : "=r"(done)
-                             : "r"(smem_addr(bar)), "r"(phase));
+            if (wait_test) {   // non-blocking polls: the test's wait ends after kTcTestWaitLimit of them
+                for (uint32_t it = 0; it < kTcTestWaitLimit && !done; ++it) {
+                    asm volatile("{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                                 : "=r"(done)
+                                 : "r"(smem_addr(bar)), "r"(phase));
+                }
+            } else {
+                for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it) {
+                    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                                 : "=r"(done)
+                                 : "r"(smem_addr(bar)), "r"(phase));
+                }
             }
         }
         phase ^= 1u;

@@ -68,3 +68,7 @@ def test_schedule_calls_reject_null_plan():
     assert L.fcc_dct_set_schedule(None, 0, 32) == binding.FCC_ERR_INVALID_ARG
     assert L.fcc_dct_get_schedule(None, 0) == -1
     assert L.fcc_dct_autotune(None, None, None, None, 3, None) == binding.FCC_ERR_INVALID_ARG
+
+
+def test_wait_timeout_hook_rejects_null_plan():
+    assert binding.lib().fcc_dct_test_wait_timeout(None, 1) == binding.FCC_ERR_INVALID_ARG

@@ -143,3 +143,24 @@ def test_launch_count_matches_recorded_launches(case):
         rec = p.profile_read()
         p.profile(False)
         assert sum(c for _, c in rec.values()) == p.launches(which), rec
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_context_survives():
+    """The bounded MMA-completion wait runs out (test hook: no MMA, no signal):
+    the host reads FCC_ERR_TIMEOUT, and the next call is correct."""
+    n, batch = 32, 4
+    L = binding.lib()
+    x = torch.from_numpy(inputs.phantom(n, batch, seed=8).astype(np.float32)).to(DEV)
+    with binding.Plan(n, batch, "r32_bf16x3") as p:
+        ref = p.forward(x).clone()
+        assert L.fcc_dct_check(p.handle) == binding.FCC_OK
+        assert L.fcc_dct_test_wait_timeout(p.handle, 1) == binding.FCC_OK
+        p.forward(x)
+        assert L.fcc_dct_check(p.handle) == binding.FCC_ERR_TIMEOUT
+        assert L.fcc_dct_check(p.handle) == binding.FCC_OK   # the status word was cleared
+        assert L.fcc_dct_test_wait_timeout(p.handle, 0) == binding.FCC_OK
+        y = p.forward(x)
+        assert L.fcc_dct_check(p.handle) == binding.FCC_OK
+        assert torch.equal(y, ref)
+    with binding.Plan(n, batch, "r32") as q:
+        assert L.fcc_dct_test_wait_timeout(q.handle, 1) == binding.FCC_ERR_UNSUPPORTED
