@@ -430,10 +430,10 @@ fcc_status launch_fft(const OrderTables& t, const T* in, T* out, int64_t nvol, i
     if (axis == 2) tiles = (nvol * n * n + a.P - 1) / a.P;
     else tiles = nvol * n * ((n + a.P - 1) / a.P);
     const size_t smem = (size_t)(4 * a.P * (n + 1) + 2 * n) * sizeof(T);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(T) == 8]) {
+    static DeviceOnce attr;   // one per instantiation of this function template
+    if (!attr.done()) {
         cudaFuncSetAttribute(fft_axis_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set[sizeof(T) == 8] = true;
+        attr.mark();
     }
     if (tiles > 0x7fffffffLL) return FCC_ERR_UNSUPPORTED;
     static const char* names[3] = {"fft_axis0", "fft_axis1", "fft_axis2"};
@@ -488,10 +488,10 @@ fcc_status fast_fft(int n, bool slab, int sign, const float2* in, float2* out, i
 }
 
 // Dynamic shared memory limits of every instantiation of mix_tiled_kernel
-// (set once per process, before the first launch of any of them).
+// (set once per device, before the first launch of any of them).
 void set_mix_tiled_attributes() {
-    static bool attr = false;
-    if (attr) return;
+    static DeviceOnce attr;
+    if (attr.done()) return;
     const int lim = 200 * 1024;
     cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -502,7 +502,7 @@ void set_mix_tiled_attributes() {
     cudaFuncSetAttribute(mix_tiled_kernel<MODE_FWD, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(mix_tiled_kernel<MODE_INV, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(mix_tiled_kernel<MODE_ADJ, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    attr = true;
+    attr.mark();
 }
 
 // which: 0 = every tile, 1 = free tiles only, 2 = boundary tiles only
@@ -678,11 +678,11 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
     const bool bf16 = p->dtype == FCC_R32_BF16X3;
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
     set_mix_tiled_attributes();
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<0>::smem);
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<1>::smem);
-        attr = true;
+        attr.mark();
     }
     for (int64_t v0 = 0; v0 < np; v0 += 65535) {
         const int64_t nv = std::min<int64_t>(65535, np - v0);

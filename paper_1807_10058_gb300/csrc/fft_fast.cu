@@ -13,13 +13,13 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
     using L = FastLayout<N>;
     // 16-byte accesses: refuse (without launching) bases that are not aligned
     if (((((uintptr_t)in) | ((uintptr_t)out)) & 15u) != 0 || (!voff && vstride % 2 != 0)) return cudaErrorMisalignedAddress;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
         cudaFuncSetAttribute(fft_slab_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
         cudaFuncSetAttribute(fft_slab_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::slab_smem);
         cudaFuncSetAttribute(fft_pencil_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
         cudaFuncSetAttribute(fft_pencil_kernel<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-        attr = true;
+        attr.mark();
     }
     if (slab) {
         const int64_t g = nvol * N;
@@ -40,10 +40,10 @@ cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const f
                           cudaStream_t st) {
     using L = FastLayout<N>;
     if (vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
         cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-        attr = true;
+        attr.mark();
     }
     const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -54,10 +54,10 @@ cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const f
 template <int N>
 cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const float2* tw, cudaStream_t st) {
     using L = FastLayout<N>;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceOnce attr;
+    if (!attr.done()) {
         cudaFuncSetAttribute(fft_pencil_merge_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-        attr = true;
+        attr.mark();
     }
     const int64_t n3 = (int64_t)N * N * N;
     const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;

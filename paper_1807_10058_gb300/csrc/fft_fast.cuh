@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "dft_reg.cuh"
 
 namespace fcc {
@@ -38,6 +40,20 @@ FCC_SHAPE(24, 12, 2)
 FCC_SHAPE(16, 4, 4)
 FCC_SHAPE(8, 4, 2)
 #undef FCC_SHAPE
+
+// Kernel attributes (dynamic shared-memory limits) are per device: a bit per
+// device id records that they are set.  Concurrent first calls may set them
+// twice (harmless); none launches before its own device's bit is set.
+struct DeviceOnce {
+    std::atomic<unsigned long long> bits{0};
+    static int dev() {
+        int d = 0;
+        cudaGetDevice(&d);
+        return d & 63;
+    }
+    bool done() const { return (bits.load() >> dev()) & 1ull; }
+    void mark() { bits.fetch_or(1ull << dev()); }
+};
 
 constexpr int kFastThreads = 256;            // pencil kernel
 constexpr int kFastWarps = kFastThreads / 32;
