@@ -103,9 +103,12 @@ fcc_status fcc_dct_adjoint(fcc_plan* plan, const void* in, void* out, void* stre
 
 /*
  * End-to-end forms taking HOST buffers: copy `host_in` to plan-owned device
- * memory, transform, copy the result to `host_out`, all enqueued on
- * `stream`.  The caller synchronises `stream` before reading host_out.
- * Pinned (page-locked) host buffers make the copies asynchronous.
+ * memory, transform, copy the result to `host_out`, all ordered after the
+ * work already on `stream`.  The caller synchronises `stream` before reading
+ * host_out.  Pinned (page-locked) host buffers make the copies asynchronous;
+ * for uniform plans of 4 or more volumes the copies of ~128 MB chunks of
+ * volumes run on two plan-owned streams, overlapping the transform of the
+ * neighbouring chunks (results are identical to the device-pointer calls).
  */
 fcc_status fcc_dct_forward_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
 fcc_status fcc_dct_inverse_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);

@@ -253,6 +253,15 @@ class Plan:
             raise ValueError("adjoint input must be %s with %d elements" % (ct, self.points))
         return self._call(lib().fcc_dct_adjoint, "fcc_dct_adjoint", g, out, not self.real_input)
 
+    def inverse_host(self, y_host, x_host):
+        """End-to-end inverse with host tensors (see forward_host)."""
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        _check(lib().fcc_dct_inverse_host(self.handle, ctypes.c_void_p(y_host.data_ptr()),
+                                          ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(st)),
+               "fcc_dct_inverse_host")
+        return x_host
+
     def forward_host(self, x_host, y_host):
         """End-to-end call with host tensors (pinned for async copies); the
         caller synchronises the current stream before reading y_host."""

@@ -91,6 +91,8 @@ struct fcc_plan {
     int64_t scratch_points = 0;
     void* host_in_dev = nullptr;     // device staging for the *_host entry points
     void* host_out_dev = nullptr;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;   // *_host: copies overlapping the transform
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_host = nullptr;
     std::vector<void*> allocs;
     // chunked schedule: volumes per chunk and internal streams (fork / join
     // with the caller's stream through events)
@@ -284,6 +286,10 @@ void release(fcc_plan* p) {
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->bnd_ev) cudaEventDestroy(p->bnd_ev);
     if (p->bnd_join) cudaEventDestroy(p->bnd_join);
+    for (cudaEvent_t e : {p->ev_in, p->ev_out, p->ev_host})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t q : {p->copy_in, p->copy_out})
+        if (q) cudaStreamDestroy(q);
     if (p->bnd_stream) cudaStreamDestroy(p->bnd_stream);
     for (auto e : p->event_pool) cudaEventDestroy(e);
     cudaSetDevice(cur);
@@ -355,6 +361,10 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
         if (s == FCC_OK && cudaEventCreateWithFlags(&p->bnd_ev, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
         if (s == FCC_OK && cudaEventCreateWithFlags(&p->bnd_join, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
         if (s == FCC_OK && cudaStreamCreateWithFlags(&p->bnd_stream, cudaStreamNonBlocking) != cudaSuccess) s = FCC_ERR_CUDA;
+        for (cudaStream_t* q : {&p->copy_in, &p->copy_out})
+            if (s == FCC_OK && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) s = FCC_ERR_CUDA;
+        for (cudaEvent_t* e : {&p->ev_in, &p->ev_out, &p->ev_host})
+            if (s == FCC_OK && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) s = FCC_ERR_CUDA;
     }
     if (s == FCC_OK) {
         // workspace for inverse / adjoint: one chunk per internal stream
@@ -957,6 +967,46 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
     return s == FCC_OK ? FCC_OK : fail(s);
 }
 
+// Uniform plans: chunks of ~128 MB of volumes go through three streams -- the
+// copy in (copy_in), the transform (the caller's stream, forking as usual)
+// and the copy out (copy_out) -- so chunk c + 1 arrives and chunk c - 1
+// leaves while chunk c is transformed.  Each event is waited on right after
+// it is recorded, so one event per direction serves every chunk.
+template <typename T>
+fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hout, cudaStream_t st) {
+    const int n = p->orders[0];
+    const OrderTables& t = p->tabs.at(n);
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
+    const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
+    const int64_t vin = n3 * rs_in * (int64_t)sizeof(T), vout = n3 * rs_out * (int64_t)sizeof(T);
+    int64_t cv = std::max<int64_t>(2, (128ll << 20) / std::max(vin, vout));
+    cv += cv % 2;   // whole pairs of real volumes
+    char* din = (char*)p->host_in_dev;
+    char* dout = (char*)p->host_out_dev;
+    if (cudaEventRecord(p->ev_host, st) != cudaSuccess || cudaStreamWaitEvent(p->copy_in, p->ev_host, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(p->copy_out, p->ev_host, 0) != cudaSuccess)
+        return FCC_ERR_CUDA;
+    fcc_status s = FCC_OK;
+    for (int64_t v0 = 0; v0 < p->batch && !s; v0 += cv) {
+        const int64_t nv = std::min<int64_t>(cv, p->batch - v0);
+        if (cudaMemcpyAsync(din + v0 * vin, hin + v0 * vin, nv * vin, cudaMemcpyHostToDevice, p->copy_in) != cudaSuccess ||
+            cudaEventRecord(p->ev_in, p->copy_in) != cudaSuccess || cudaStreamWaitEvent(st, p->ev_in, 0) != cudaSuccess) {
+            s = FCC_ERR_CUDA;
+            break;
+        }
+        s = run_group<T>(p, which, t, (const T*)(din + v0 * vin), (T*)(dout + v0 * vout), nv, st);
+        if (s) break;
+        if (cudaEventRecord(p->ev_out, st) != cudaSuccess || cudaStreamWaitEvent(p->copy_out, p->ev_out, 0) != cudaSuccess ||
+            cudaMemcpyAsync(hout + v0 * vout, dout + v0 * vout, nv * vout, cudaMemcpyDeviceToHost, p->copy_out) != cudaSuccess)
+            s = FCC_ERR_CUDA;
+    }
+    // the caller's stream completes after the last copy out
+    if (cudaEventRecord(p->ev_host, p->copy_out) != cudaSuccess || cudaStreamWaitEvent(st, p->ev_host, 0) != cudaSuccess)
+        return FCC_ERR_CUDA;
+    return s;
+}
+
 fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream) {
     if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
     cudaStream_t st = (cudaStream_t)stream;
@@ -966,6 +1016,17 @@ fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, vo
     fcc_status s;
     if (!p->host_in_dev && (s = dev_alloc(p, &p->host_in_dev, cap))) return fail(s);
     if (!p->host_out_dev && (s = dev_alloc(p, &p->host_out_dev, capo))) return fail(s);
+    if (p->uniform && p->batch >= 4) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+        if (cur != p->device) cudaSetDevice(p->device);
+        g_prof_plan = p;
+        s = is_double(p->dtype) ? run_host_pipelined<double>(p, which, (const char*)hin, (char*)hout, st)
+                                : run_host_pipelined<float>(p, which, (const char*)hin, (char*)hout, st);
+        g_prof_plan = nullptr;
+        if (cur != p->device) cudaSetDevice(cur);
+        return s == FCC_OK ? FCC_OK : fail(s);
+    }
     if (cudaMemcpyAsync(p->host_in_dev, hin, ib, cudaMemcpyHostToDevice, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
     if ((s = dispatch(p, which, p->host_in_dev, p->host_out_dev, stream))) return s;
     if (cudaMemcpyAsync(hout, p->host_out_dev, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
