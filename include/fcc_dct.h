@@ -170,7 +170,10 @@ fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, voi
  * failure of the plan's earlier calls: FCC_ERR_TIMEOUT if a bounded wait of a
  * tensor-core kernel gave up (the kernel then skipped its remaining work and
  * released its tensor memory), FCC_ERR_CUDA if a launch or the device
- * failed.  Clears the plan's device status word.
+ * failed.  Clears the plan's status word.  The word lives in pinned host
+ * memory, so the plan's next forward / inverse / adjoint call also returns
+ * FCC_ERR_TIMEOUT (without launching, and clearing it) once a kernel of an
+ * earlier call has recorded a timeout.
  */
 fcc_status fcc_dct_check(fcc_plan* plan);
 

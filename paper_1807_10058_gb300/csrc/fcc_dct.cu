@@ -105,7 +105,10 @@ struct fcc_plan {
     int wait_test = 0;               // fcc_dct_test_wait_timeout
     int scratch_streams = 1;         // internal streams the inverse / adjoint workspace was sized for
     int num_sms = 1;
-    int* d_status = nullptr;         // device-side wait timeouts (tensor-core kernels)
+    // device-side wait timeouts of the tensor-core kernels: a word of pinned,
+    // mapped host memory, so that the host reads it without a device sync
+    int* h_status = nullptr;
+    int* d_status = nullptr;         // its device address
     cudaStream_t streams[kMaxStreams] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t bnd_ev = nullptr;    // boundary tiles done (forward)
@@ -286,6 +289,7 @@ void release(fcc_plan* p) {
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->bnd_ev) cudaEventDestroy(p->bnd_ev);
     if (p->bnd_join) cudaEventDestroy(p->bnd_join);
+    if (p->h_status) cudaFreeHost(p->h_status);
     for (cudaEvent_t e : {p->ev_in, p->ev_out, p->ev_host})
         if (e) cudaEventDestroy(e);
     for (cudaStream_t q : {p->copy_in, p->copy_out})
@@ -321,9 +325,16 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
     cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
     if (p->num_sms < 1) p->num_sms = 1;
     fcc_status s = upload_group();
-    if (s == FCC_OK && (s = dev_alloc(p, (void**)&p->d_status, sizeof(int))) == FCC_OK &&
-        cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
-        s = FCC_ERR_CUDA;
+    if (s == FCC_OK) {
+        if (cudaHostAlloc((void**)&p->h_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            p->h_status = nullptr;
+            s = FCC_ERR_ALLOC;
+        } else {
+            *(volatile int*)p->h_status = 0;
+            if (cudaHostGetDevicePointer((void**)&p->d_status, p->h_status, 0) != cudaSuccess) s = FCC_ERR_CUDA;
+        }
+    }
     for (int n : orders) {
         if (s != FCC_OK) break;
         if (p->tabs.count(n)) continue;
@@ -952,6 +963,12 @@ fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t
 
 fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* stream) {
     if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    // a device-side timeout of an earlier call surfaces here (the word is
+    // host memory; a call still running may set it later)
+    if (*(volatile int*)p->h_status != 0) {
+        *(volatile int*)p->h_status = 0;
+        return fail(FCC_ERR_TIMEOUT);
+    }
     if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, which);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, which);
@@ -1273,13 +1290,12 @@ fcc_status fcc_dct_check(fcc_plan* p) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
-    int st = 0;
     fcc_status s = FCC_OK;
-    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaGetLastError();
         s = FCC_ERR_CUDA;
-    } else if (st != 0) {
-        cudaMemset(p->d_status, 0, sizeof(int));
+    } else if (*(volatile int*)p->h_status != 0) {
+        *(volatile int*)p->h_status = 0;
         s = FCC_ERR_TIMEOUT;
     }
     if (cur != p->device) cudaSetDevice(cur);

@@ -329,7 +329,10 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         phase ^= 1u;
         // block-uniform decision: every thread must take the same path below
         if (!__syncthreads_and((int)done)) {
-            if (tid == 0) atomicExch(status, 1);
+            if (tid == 0) {   // host-mapped word: a plain store made visible system-wide
+                *(volatile int*)status = 1;
+                __threadfence_system();
+            }
             ok = false;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");

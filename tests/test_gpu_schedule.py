@@ -158,6 +158,13 @@ def test_tensor_core_wait_timeout_is_reported_and_the_context_survives():
         p.forward(x)
         assert L.fcc_dct_check(p.handle) == binding.FCC_ERR_TIMEOUT
         assert L.fcc_dct_check(p.handle) == binding.FCC_OK   # the status word was cleared
+        # the plan's next call reports a timeout recorded by an earlier one
+        p.forward(x)
+        torch.cuda.synchronize()
+        with pytest.raises(binding.FccError) as e:
+            p.forward(x)
+        assert e.value.status == binding.FCC_ERR_TIMEOUT
+        assert L.fcc_dct_check(p.handle) == binding.FCC_OK
         assert L.fcc_dct_test_wait_timeout(p.handle, 0) == binding.FCC_OK
         y = p.forward(x)
         assert L.fcc_dct_check(p.handle) == binding.FCC_OK
