@@ -56,46 +56,9 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // Compile-time entries of W (read only in constant expressions).
-template <int G, int I> struct WM { static constexpr int v = wc::K::t.m[G][I]; };
 template <int G, int I> struct WU { static constexpr int v = wc::K::t.u[G][I]; };
-template <int G, int I> struct WF { static constexpr int v = wc::K::t.fw[G][I]; };
 template <int G> struct WD { static constexpr int v = wc::K::t.dir[G]; };
 
-template <int G>
-__device__ __forceinline__ void slot_point(uint32_t rp, int& p0, int& p1, int& p2) {
-    const int k0 = rp & 1023, k1 = (rp >> 10) & 1023, k2 = (rp >> 20) & 1023;
-    p0 = WM<G, 0>::v * k0 + WM<G, 1>::v * k1 + WM<G, 2>::v * k2;
-    p1 = WM<G, 3>::v * k0 + WM<G, 4>::v * k1 + WM<G, 5>::v * k2;
-    p2 = WM<G, 6>::v * k0 + WM<G, 7>::v * k1 + WM<G, 8>::v * k2;
-}
-
-// flat index of slot G of representative rp for a free orbit (compile-time wrap)
-template <int G>
-__device__ __forceinline__ int slot_idx_free(uint32_t rp, int n) {
-    int p0, p1, p2;
-    slot_point<G>(rp, p0, p1, p2);
-    p0 -= n * WF<G, 0>::v;
-    p1 -= n * WF<G, 1>::v;
-    p2 -= n * WF<G, 2>::v;
-    return (p0 * n + p1) * n + p2;
-}
-
-template <int G>
-__device__ __forceinline__ int slot_idx_gen(uint32_t rp, const int8_t* wr, int n) {
-    int p0, p1, p2;
-    slot_point<G>(rp, p0, p1, p2);
-    p0 -= n * wr[3 * G + 0];
-    p1 -= n * wr[3 * G + 1];
-    p2 -= n * wr[3 * G + 2];
-    return (p0 * n + p1) * n + p2;
-}
-
-template <int G>
-__device__ __forceinline__ int slot_phase(uint32_t rp, int M8) {
-    const int k0 = rp & 1023, k1 = (rp >> 10) & 1023, k2 = (rp >> 20) & 1023;
-    int e = (WU<G, 0>::v * k0 + WU<G, 1>::v * k1 + WU<G, 2>::v * k2) % M8;
-    return e < 0 ? e + M8 : e;
-}
 
 constexpr int kMixWarps = 8;                 // warps (= independent tiles) per block
 constexpr int kMixThreads = 32 * kMixWarps;
