@@ -534,7 +534,7 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
                         int64_t in_vstride, int64_t out_vstride) {
     using L = FastLayout<N>;
     using P = PairLayout<N>;
-    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
+    constexpr int R1 = L::R1, G = L::G, PPW = L::PPW;
     constexpr int ROWS = N / 2 + 1;
     constexpr int64_t NN = (int64_t)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
