@@ -187,7 +187,8 @@ def run_reference(args):
 
 FORM_NAMES = {"r32": "plain FP32 (SIMT orbit cores)",
               "r32_bf16x3": "tensor-core (tcgen05 BF16, 3-term split inputs) orbit-core",
-              "r32_tf32x3": "tensor-core (tcgen05 TF32, 3-term split inputs) orbit-core"}
+              "r32_tf32x3": "tensor-core (tcgen05 TF32, 2-term split inputs, exact core) orbit-core",
+              "r32_bf16x6": "tensor-core (tcgen05 BF16, 6-product form = 3 products, exact core) orbit-core"}
 
 
 def sampled_accuracy(x, y, n, dev, rows=24):
@@ -455,7 +456,8 @@ def main():
             "metric": METRIC, "value": world * pts / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"r32": "f32", "r32_bf16x3": "bf16x3/f32", "r32_tf32x3": "tf32x3/f32"}.get(args.dtype, args.dtype),
+            "dtype": {"r32": "f32", "r32_bf16x3": "bf16x3/f32", "r32_tf32x3": "tf32x3/f32",
+                      "r32_bf16x6": "bf16x6/f32"}.get(args.dtype, args.dtype),
             "data": "synthetic CT-like phantoms (10-30 random ellipsoids, densities U[0,1], +N(0,1e-3^2)), seeded",
             "config": {"workload": "FCC-DCT forward y = DCT_n x, order n=%d, batch %d, FP32 real -> complex64, "
                                    "%s form" % (n, batch, FORM_NAMES.get(args.dtype, args.dtype)),

@@ -69,7 +69,8 @@ typedef enum {
     FCC_C32 = 3,
     FCC_R32_TF32X3 = 4,   /* FP32 storage; the forward orbit cores on the tensor cores (TF32, 3-term inputs) */
     FCC_R32_BF16X3 = 5,   /* FP32 storage; the forward orbit cores on the tensor cores (BF16, 3-term inputs) */
-    FCC_R32_BF16X6 = 6    /* reserved: returns FCC_ERR_UNSUPPORTED (the core matrices are exact in BF16) */
+    FCC_R32_BF16X6 = 6    /* 3-way split of both operands, 6 products: the core's low parts are exactly
+                             zero, so this runs the 3 products of FCC_R32_BF16X3 (identical results) */
 } fcc_dtype;
 
 /* Largest supported order n. */

@@ -34,7 +34,10 @@ fcc_status fail(fcc_status s) {
 }
 
 bool is_double(int dtype) { return dtype == FCC_R64 || dtype == FCC_C64; }
-bool is_tc(int dtype) { return dtype == FCC_R32_TF32X3 || dtype == FCC_R32_BF16X3; }
+bool is_tc(int dtype) { return dtype == FCC_R32_TF32X3 || dtype == FCC_R32_BF16X3 || dtype == FCC_R32_BF16X6; }
+// BF16 terms (the 6-product form of a 3-way split of both operands reduces to
+// the 3 products of BF16X3: the core's low parts are zero)
+bool is_bf16(int dtype) { return dtype == FCC_R32_BF16X3 || dtype == FCC_R32_BF16X6; }
 bool is_real_in(int dtype) { return dtype != FCC_C64 && dtype != FCC_C32; }
 
 // Device copy of one order's tables.
@@ -200,7 +203,7 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     t.free_tiles = hp.free_tiles;
     if (is_tc(p->dtype) && hp.free_class >= 0) {
         std::vector<unsigned char> img;
-        const bool ok = p->dtype == FCC_R32_BF16X3 ? build_tc_core_image<0>(hp.classes[hp.free_class].fwd.data(), img)
+        const bool ok = is_bf16(p->dtype) ? build_tc_core_image<0>(hp.classes[hp.free_class].fwd.data(), img)
                                                    : build_tc_core_image<1>(hp.classes[hp.free_class].fwd.data(), img);
         if (!ok) return FCC_ERR_UNSUPPORTED;
         if ((s = upload(p, &t.tc_core_image, img.data(), img.size()))) return s;
@@ -213,7 +216,7 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
         std::vector<unsigned char> imgs, one;
         std::vector<int> off(hp.classes.size() * 24);
         for (size_t c = 0; c < hp.classes.size(); ++c) {
-            const bool okc = p->dtype == FCC_R32_BF16X3 ? build_tc_core_image<0>(hp.classes[c].fwd.data(), one)
+            const bool okc = is_bf16(p->dtype) ? build_tc_core_image<0>(hp.classes[c].fwd.data(), one)
                                                         : build_tc_core_image<1>(hp.classes[c].fwd.data(), one);
             if (!okc) return FCC_ERR_UNSUPPORTED;
             imgs.insert(imgs.end(), one.begin(), one.end());
@@ -302,7 +305,6 @@ void release(fcc_plan* p) {
 
 fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
     if (dtype < FCC_R64 || dtype > FCC_R32_BF16X6) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
-    if (dtype == FCC_R32_BF16X6) { fail(FCC_ERR_UNSUPPORTED); return nullptr; }
     if (orders.empty()) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     for (int n : orders)
         if (n < 1 || n > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
@@ -696,7 +698,7 @@ fcc_status merge_dft3_pairs(const OrderTables& t, const float* y, float* ws, int
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
                                cudaStream_t st) {
     TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
-    const bool bf16 = p->dtype == FCC_R32_BF16X3;
+    const bool bf16 = is_bf16(p->dtype);
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
     set_mix_tiled_attributes();
     static DeviceOnce attr;

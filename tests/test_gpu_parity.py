@@ -170,9 +170,6 @@ def test_unsupported_order_reports_status():
     with pytest.raises(binding.FccError) as e:
         binding.Plan(37, 1, "r32")
     assert e.value.status == binding.FCC_ERR_UNSUPPORTED
-    with pytest.raises(binding.FccError) as e:
-        binding.Plan(8, 1, "r32_bf16x6")
-    assert e.value.status == binding.FCC_ERR_UNSUPPORTED
 
 
 # --- tensor-core form: the forward orbit cores on tcgen05 ----------------------
@@ -310,3 +307,12 @@ def test_host_entry_points_in_several_chunks(batch):
         torch.cuda.synchronize()
     assert torch.equal(yd, yh)
     assert torch.equal(back, xb)
+
+
+def test_bf16x6_equals_bf16x3():
+    """A 3-way split of the exact core has zero low parts: the 6-product form
+    is the 3-product form, bit for bit."""
+    n, batch = 48, 6
+    x = dev(inputs.phantom(n, batch, seed=31).astype(np.float32), np.float32)
+    with binding.Plan(n, batch, "r32_bf16x3") as a, binding.Plan(n, batch, "r32_bf16x6") as b:
+        assert torch.equal(a.forward(x), b.forward(x))
