@@ -17,6 +17,7 @@
 #include "fft_fast.cuh"
 #include "kernels.cuh"
 #include "mix_tc.cuh"
+#include "mix_tc_inv.cuh"
 #include "ragged.cuh"
 #include "mix_tiled.cuh"
 #include "pair.cuh"
@@ -72,6 +73,8 @@ struct OrderTables {
     int* tc_off = nullptr;
     int* tc_bgroups = nullptr;
     int tc_nbgroups = 0;
+    // inverse / adjoint blocks of every class, three BF16 terms each (six-product form)
+    void* tc_inv_images[2] = {nullptr, nullptr};
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
@@ -231,6 +234,14 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
             groups.insert(groups.end(), grp, grp + 8);
         }
         t.tc_nbgroups = (int)(groups.size() / 8);
+        for (int md = 0; md < 2; ++md) {
+            std::vector<unsigned char> all;
+            for (size_t c = 0; c < hp.classes.size(); ++c) {
+                build_tc_inv_image(md == 0 ? hp.classes[c].inv.data() : hp.classes[c].adj.data(), one);
+                all.insert(all.end(), one.begin(), one.end());
+            }
+            if ((s = upload(p, &t.tc_inv_images[md], all.data(), all.size()))) return s;
+        }
         if ((s = upload(p, &t.tc_core_images, imgs.data(), imgs.size()))) return s;
         if ((s = upload(p, (void**)&t.tc_off, off.data(), off.size() * 4))) return s;
         if (!groups.empty() && (s = upload(p, (void**)&t.tc_bgroups, groups.data(), groups.size() * 4))) return s;
@@ -736,6 +747,32 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
 }
 
+// Inverse / adjoint mixing of `np` pairs on the tensor cores: compact complex
+// W (pair p at p n^3 of in) -> real volumes 2p, 2p + 1 of out.
+fcc_status launch_mix_tc_inv_pairs(const fcc_plan* p, const OrderTables& t, int mode, const float* in, float* out,
+                                   int64_t np, float scale, cudaStream_t st) {
+    TiledMixArgs a = make_mix_args(t, mode, scale);
+    const int md = mode == MODE_INV ? 0 : 1;
+    static DeviceOnce attr;
+    if (!attr.done()) {
+        cudaFuncSetAttribute(mix_tc_inv_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcInvLayout::smem);
+        attr.mark();
+    }
+    const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups, (const uint4*)t.tc_inv_images[md], t.tc_off, t.canon_mask};
+    const uint4* free_image = (const uint4*)((const unsigned char*)t.tc_inv_images[md] + (size_t)t.free_class * TcInvLayout::image_bytes);
+    for (int64_t v0 = 0; v0 < np; v0 += 65535) {
+        const int64_t nv = std::min<int64_t>(65535, np - v0);
+        const int ngroups = (t.free_tiles + 3) / 4 + t.tc_nbgroups;
+        const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, 3) : 3;   // 80 registers: 3 blocks per SM
+        const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
+        ProfScope ps(mode == MODE_INV ? "mix_tc_inv" : "mix_tc_adj", st);
+        mix_tc_inv_pair_kernel<<<dim3((unsigned)gx, (unsigned)nv), kTcThreads, TcInvLayout::smem, st>>>(
+            (const float2*)in + v0 * a.n3, out + v0 * a.n3 * 2, a, t.free_tiles, t.tc_reps32, free_image, scale,
+            p->d_status, bnd, p->wait_test);
+    }
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
 int64_t chunk_vols(const fcc_plan* p, int n) {
     const int64_t n3 = (int64_t)n * n * n;
     return std::max<int64_t>(1, p->chunk_bytes / (n3 * 8));
@@ -792,7 +829,8 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             float* x = out + 2 * p0 * n3;
             s = merge_dft3_pairs(t, y, ws, np, ss);
             const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
-            if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, true, ws, x, np, scale, ss, true);
+            if (!s && tc_all) s = launch_mix_tc_inv_pairs(p, t, which == 1 ? MODE_INV : MODE_ADJ, ws, x, np, scale, ss);
+            else if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, true, ws, x, np, scale, ss, true);
         }
     }
     for (int64_t v0 = 2 * npairs; v0 < nvol && !s; v0 += cv, ++c) {
@@ -1230,7 +1268,7 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
                 const int64_t np = std::min(cv, npairs - p0);
                 // (the inverse / adjoint merge into a compact workspace first)
                 const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
-                total += (int)((split_b || (tc_all && which == 0) ? 1 : mixl) + dft_pair);
+                total += (int)((split_b || tc_all ? 1 : mixl) + dft_pair);
             }
             const int64_t rest = nv - 2 * npairs;
             total += (int)(((rest + cv - 1) / cv) * (mixl + dft));

@@ -316,3 +316,30 @@ def test_bf16x6_equals_bf16x3():
     x = dev(inputs.phantom(n, batch, seed=31).astype(np.float32), np.float32)
     with binding.Plan(n, batch, "r32_bf16x3") as a, binding.Plan(n, batch, "r32_bf16x6") as b:
         assert torch.equal(a.forward(x), b.forward(x))
+
+
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32_tf32x3", "r32_bf16x6"])
+@pytest.mark.parametrize("n,batch", [(8, 4), (16, 3), (24, 2), (48, 4), (64, 2)])
+def test_tensor_core_inverse_and_adjoint(dtype, n, batch):
+    """Inverse and adjoint of the tensor-core dtypes: the class blocks on
+    tcgen05 in the six-product BF16 form (FP32-level accuracy).  The adjoint
+    against the oracle's D^H; the inverse against the exact inverse of the
+    same complex64 input (dense oracle at n <= 16) or, beyond, against the
+    plain FP32 inverse and the original volume."""
+    x = inputs.smoothed_noise(n, batch, seed=17).astype(np.float32)
+    ref = oracle.forward_sum_fft(x.astype(np.float64), n)
+    y32 = ref.astype(np.complex64)
+    g = (inputs.uniform(n, batch, seed=18) + 1j * inputs.uniform(n, batch, seed=19)).astype(np.complex64)
+    with binding.Plan(n, batch, dtype) as p:
+        xi = host(p.inverse(dev(y32, np.complex64)), x.shape)
+        ad = host(p.adjoint(dev(g, np.complex64)), x.shape)
+        p.check()
+    with binding.Plan(n, batch, "r32") as q:
+        xi32 = host(q.inverse(dev(y32, np.complex64)), x.shape)
+    aref = oracle.adjoint_sum_fft(g.astype(np.complex128), n).real
+    assert rel(ad, aref) < TC_TOL, rel(ad, aref)
+    if n <= 16:
+        xref = np.stack([oracle.inverse_dense(y32[b].astype(np.complex128), n).real for b in range(batch)])
+        assert rel(xi, xref) < TC_TOL, rel(xi, xref)
+    assert rel(xi, xi32) < 2e-6, rel(xi, xi32)
+    assert rel(xi, x) < 4e-5

@@ -123,7 +123,8 @@ def test_autotune_keeps_a_valid_schedule(ragged):
         assert rel(y, y0) < 1e-6
 
 
-@pytest.mark.parametrize("case", ["r32_n128", "bf16_n64", "ragged", "ragged_persistent", "inverse", "odd_n", "odd_n_inverse"])
+@pytest.mark.parametrize("case", ["r32_n128", "bf16_n64", "ragged", "ragged_persistent", "inverse", "odd_n", "odd_n_inverse",
+                                  "bf16_inverse"])
 def test_launch_count_matches_recorded_launches(case):
     if case.startswith("ragged"):
         orders = inputs.ragged_orders(12, seed=2)
@@ -132,7 +133,7 @@ def test_launch_count_matches_recorded_launches(case):
             p.set_schedule(ragged=1)
     else:
         n, batch, dtype = {"r32_n128": (128, 5, "r32"), "bf16_n64": (64, 9, "r32_bf16x3"), "inverse": (64, 6, "r32"),
-                           "odd_n": (27, 5, "r32"), "odd_n_inverse": (27, 5, "r32")}[case]
+                           "odd_n": (27, 5, "r32"), "odd_n_inverse": (27, 5, "r32"), "bf16_inverse": (64, 7, "r32_bf16x3")}[case]
         p = binding.Plan(n, batch, dtype)
     with p:
         which = 1 if case.endswith("inverse") else 0
