@@ -245,6 +245,13 @@ def secondary_configs(dev):
         rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
     out["roundtrip_n64_b256"] = {"value": b * n ** 3 / (ms * 1e-3) / 1e9, "unit": "Gpoints/s (forward + inverse)",
                                  "ms_per_step": ms, "roundtrip_rel_l2": rt, "data": "i.i.d. N(0,1) coefficients"}
+    # the same round trip in the tensor-core form (context: its inverse runs the
+    # six-product BF16 blocks)
+    with binding.Plan(n, b, "r32_bf16x3") as p:
+        ms = _time(lambda: (p.forward(x, out=y), p.inverse(y, out=xr)), 5, 3)
+        rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
+    out["roundtrip_n64_b256_tensor_core"] = {"value": b * n ** 3 / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                                             "roundtrip_rel_l2": rt, "form": "r32_bf16x3"}
     # ragged, 1000 volumes: per-order launches and the single persistent
     # launch, each captured in a CUDA graph; one launch set per run of equal
     # orders (no graph); then the autotuner's pick
