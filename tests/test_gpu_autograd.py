@@ -39,13 +39,15 @@ def test_masked_reconstruction_gradient_matches_oracle():
     assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-12
 
 
-def test_adjoint_dot_product_fp32_large():
+@pytest.mark.parametrize("dtype", ["r32", "r32_bf16x3", "r32_tf32x3"])
+def test_adjoint_dot_product_fp32_large(dtype):
     """<D x, g> = <x, Re D^H g>, the difference measured against the
-    Cauchy-Schwarz scale ||g|| ||D x|| (the inner product itself may cancel)."""
+    Cauchy-Schwarz scale ||g|| ||D x|| (the inner product itself may cancel);
+    the tensor-core forms run both the forward and the adjoint on tcgen05."""
     n, batch = 64, 2
     gen = torch.Generator(device=DEV)
     gen.manual_seed(12)
-    with binding.Plan(n, batch, "r32") as p:
+    with binding.Plan(n, batch, dtype) as p:
         x = torch.randn(batch * n ** 3, device=DEV, generator=gen)
         g = torch.randn(batch * n ** 3, device=DEV, dtype=torch.complex64, generator=gen)
         y = p.forward(x)
