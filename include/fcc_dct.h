@@ -225,8 +225,9 @@ int fcc_dct_get_schedule(const fcc_plan* plan, int key);
 /*
  * Autotuner (no counterpart in the paper): times the forward transform of
  * `in` into `out` (device buffers, the layouts of fcc_dct_forward) under the
- * candidate schedules -- chunk size x internal streams and the tensor-core
- * grid for uniform plans; per-order launches x streams, the persistent
+ * candidate schedules -- chunk size (8, 16, 32, 64 MB) x internal streams
+ * (1-4), then the tensor-core grid, for uniform plans; per-order launches x
+ * streams, the persistent
  * launch and per-run launches for ragged plans -- with one untimed call and
  * `reps` (1..100) timed calls each, keeps the fastest and writes its time per
  * call to *best_ms (if not NULL).  Synchronises `stream`; overwrites `out`.

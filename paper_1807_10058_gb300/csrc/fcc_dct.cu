@@ -1148,12 +1148,12 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
     const int tc0 = p->tc_blocks;
     if (!p->uniform) {
         const bool fast = !is_double(p->dtype) && ragged_fast_ok(p, 0);
-        for (int ns = 1; ns <= 3 && fast; ++ns) cands.push_back({32, ns, 0, tc0});
+        for (int ns = 1; ns <= kMaxStreams && fast; ++ns) cands.push_back({32, ns, 0, tc0});
         if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0});
         cands.push_back({32, 2, 2, tc0});
     } else {
-        for (int mb : {16, 32, 64})
-            for (int ns = 1; ns <= 3; ++ns) cands.push_back({mb, ns, 0, tc0});
+        for (int mb : {8, 16, 32, 64})
+            for (int ns = 1; ns <= kMaxStreams; ++ns) cands.push_back({mb, ns, 0, tc0});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
