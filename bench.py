@@ -53,21 +53,28 @@ def rank_seed(rank):
     return 1000 * int(rank)
 
 
+def kernel_sources_digest():
+    """sha256 over the files that define the kernels (csrc/*.cuh, csrc/*.h);
+    the host orchestration (*.cu, *.cpp) does not change what a kernel does."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1807_10058_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
 def _traffic(kernel, points_per_launch):
     """DRAM bytes per launch of `kernel` from the committed ncu capture
     (profiles/kernel_traffic.json), scaled to the launch size; None when the
     kernel sources changed since the capture or the kernel was not captured."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "kernel_traffic.json")) as f:
             d = json.load(f)
-        csrc = os.path.join(ROOT, "paper_1807_10058_gb300", "csrc")
-        h = hashlib.sha256()
-        for name in sorted(os.listdir(csrc)):
-            h.update(name.encode())
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != d["csrc_sha256"] or kernel not in d["kernels"]:
+        if kernel_sources_digest() != d["kernel_sources_sha256"] or kernel not in d["kernels"]:
             return None
         k = d["kernels"][kernel]
         return (k["dram_read"] + k["dram_write"]) * points_per_launch / d["points_per_launch"]
