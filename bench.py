@@ -54,16 +54,21 @@ def rank_seed(rank):
 
 
 def kernel_sources_digest():
-    """sha256 over the files that define the kernels (csrc/*.cuh, csrc/*.h);
-    the host orchestration (*.cu, *.cpp) does not change what a kernel does."""
+    """sha256 over the code of the files that define the kernels (csrc/*.cuh,
+    csrc/*.h) with comments and whitespace removed; the host orchestration
+    (*.cu, *.cpp) and the comments do not change what a kernel does."""
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_1807_10058_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cuh", ".h")):
+            with open(os.path.join(csrc, name)) as f:
+                code = f.read()
+            code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+            code = re.sub(r"//[^\n]*", " ", code)
             h.update(name.encode())
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+            h.update(" ".join(code.split()).encode())
     return h.hexdigest()
 
 

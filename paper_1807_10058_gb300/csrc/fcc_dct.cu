@@ -1,5 +1,8 @@
-// C ABI of libfccdct (declared in include/fcc_dct.h): plans, launches,
-// error handling.  All compute runs in the kernels of kernels.cuh.
+// C ABI of libfccdct (declared in include/fcc_dct.h): plans, schedules,
+// launches, error handling.  All compute runs in the kernels of the headers
+// included below (generic: kernels.cuh; tiled FP32 mixing: mix_tiled.cuh;
+// tensor-core mixing: mix_tc.cuh, mix_tc_inv.cuh; register-radix DFT passes:
+// fft_fast.cuh; pairing: pair.cuh; persistent ragged launch: ragged.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,8 +1,8 @@
 // Forward orbit mixing of paired real volumes with the orbit core on the
 // 5th-generation tensor cores (tcgen05, accumulator in tensor memory).
 //
-// For the free orbits the forward core is E / 24 with E[g][h] an 8th root of
-// unity.  In real form, with outputs (Re Z_g, Im Z_g) and inputs
+// For every orbit class the forward core is E / 24 with E[g][h] an 8th root
+// of unity.  In real form, with outputs (Re Z_g, Im Z_g) and inputs
 // (Re x_h, Im x_h), the 48 x 48 matrix has entries 0, +-1, +-1/sqrt(2); it is
 // split exactly as A1 + A2 / sqrt(2) with A1, A2 in {0, +-1}, both exact in
 // BF16 and TF32.  The FP32 inputs are split into terms of the MMA input type
@@ -22,12 +22,14 @@
 // row t of X and reads its half of TMEM lane t in the epilogue, so no
 // transpose is needed anywhere.
 //
-// Pipeline per block (4 warps = 4 tiles of the plan, <= 128 orbits): the
-// gather loads of the next tile are issued as soon as the current tile's data
-// operand is stored, so they are in flight during the barrier, the MMAs, the
-// completion wait and the epilogue.  Representatives come from a table
-// padded to 32 per plan tile (all ones = no orbit), read a tile ahead, so no
-// chain of dependent table loads precedes the gather.
+// Pipeline per block (8 warps; a block tile = 4 tiles of the plan, <= 128
+// orbits): the gather loads of the next block tile are issued as soon as the
+// current one's data operand is stored, so they are in flight during the
+// barrier, the MMAs, the completion wait and the epilogue.  Representatives
+// come from a table padded to 32 per plan tile (all ones = no orbit), read a
+// tile ahead, so no chain of dependent table loads precedes the gather.  The
+// free tiles come first, then the boundary tiles in groups of one class with
+// that class's core image, wrap offsets and canonical-slot mask.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
