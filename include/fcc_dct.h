@@ -107,7 +107,7 @@ fcc_status fcc_dct_adjoint(fcc_plan* plan, const void* in, void* out, void* stre
  * memory, transform, copy the result to `host_out`, all ordered after the
  * work already on `stream`.  The caller synchronises `stream` before reading
  * host_out.  Pinned (page-locked) host buffers make the copies asynchronous;
- * for uniform plans of 4 or more volumes the copies of ~128 MB chunks of
+ * for uniform plans of 4 or more volumes the copies of ~32 MB chunks of
  * volumes run on two plan-owned streams, overlapping the transform of the
  * neighbouring chunks (results are identical to the device-pointer calls).
  */

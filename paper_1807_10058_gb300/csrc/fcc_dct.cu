@@ -1027,7 +1027,7 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
     return s == FCC_OK ? FCC_OK : fail(s);
 }
 
-// Uniform plans: chunks of ~128 MB of volumes go through three streams -- the
+// Uniform plans: chunks of ~32 MB of volumes go through three streams -- the
 // copy in (copy_in), the transform (the caller's stream, forking as usual)
 // and the copy out (copy_out) -- so chunk c + 1 arrives and chunk c - 1
 // leaves while chunk c is transformed.  Each event is waited on right after
@@ -1040,7 +1040,7 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
     const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t vin = n3 * rs_in * (int64_t)sizeof(T), vout = n3 * rs_out * (int64_t)sizeof(T);
-    int64_t cv = std::max<int64_t>(2, (128ll << 20) / std::max(vin, vout));
+    int64_t cv = std::max<int64_t>(2, (32ll << 20) / std::max(vin, vout));
     cv += cv % 2;   // whole pairs of real volumes
     char* din = (char*)p->host_in_dev;
     char* dout = (char*)p->host_out_dev;
