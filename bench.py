@@ -203,7 +203,7 @@ FORM_NAMES = {"r32": "plain FP32 (SIMT orbit cores)",
               "r32_bf16x6": "tensor-core (tcgen05 BF16, 6-product form = 3 products, exact core) orbit-core"}
 
 
-def sampled_accuracy(x, y, n, dev, rows=24):
+def sampled_accuracy(x, y, n, dev, rows=24, skew=None):
     """Relative L2 error against the FP64 oracle, estimated from uniformly
     sampled whole rows of D on the first volume (an unbiased estimate of the
     whole-output relative L2), and the largest sampled error."""
@@ -213,7 +213,8 @@ def sampled_accuracy(x, y, n, dev, rows=24):
         import oracle
         r = np.random.default_rng(3).integers(0, n ** 3, size=rows)
         vol = x[:n ** 3].double().cpu().numpy()
-        ref = oracle.forward_rows(vol, n, r, nthreads=len(os.sched_getaffinity(0)))
+        ref = oracle.forward_rows(vol, n, r, skew=skew or oracle.CANONICAL_SKEW,
+                                  nthreads=len(os.sched_getaffinity(0)))
         got = y[torch.from_numpy(r).to(dev)].cpu().numpy()
         rms = torch.sqrt(torch.mean(torch.abs(y[:n ** 3].to(torch.complex128)) ** 2)).item()
         err = np.abs(got - ref)
@@ -241,7 +242,7 @@ def secondary_configs(dev):
     """The other workloads, each short: order 64 x 256 round trip; a ragged
     batch of 1000 volumes (orders 8..96) under each ragged schedule; order
     96 x 32 masked-reconstruction gradient descent through the autograd
-    wrapper."""
+    wrapper; the skew transform at order 128 x 64."""
     import numpy as np
     import torch
     from paper_1807_10058_gb300 import binding, inputs
@@ -323,6 +324,28 @@ def secondary_configs(dev):
         final = step().item()
     out["autograd_gd_n96_b32"] = {"ms_per_gd_step": ms_gd, "steps_timed": 50, "loss_ratio_after": final / l0,
                                   "note": "forward + adjoint backward per step, step size 1e-6"}
+    # the skew transform DCT_n(1/16, 0, 11/16) of Def. 2 (a halved shift of the
+    # radix-2 step), order 128 x 64, FP32: generic orbit mixing with the
+    # plan's row phases + the register-radix DFT passes, no pairing
+    n, b, skew = 128, 64, ((1, 0, 11), 16)
+    x = inputs.phantom_device(n, b, seed=5, device=dev)
+    y = torch.empty(b * n ** 3, dtype=torch.complex64, device=dev)
+    with binding.Plan(n, b, "r32", skew=skew) as p:
+        ms = _time(lambda: p.forward(x, out=y), 10, 3)
+        launches = p.launches(0)
+        p.profile(True)
+        p.forward(x, out=y)
+        torch.cuda.synchronize()
+        kern = {k: round(v[0], 4) for k, v in p.profile_read().items()}
+        p.profile(False)
+    pts = b * n ** 3
+    peak, kind = _peaks()
+    out["skew_n128_b64"] = {"value": pts / (ms * 1e-3) / 1e9, "unit": "Gpoints/s", "ms_per_step": ms,
+                            "shift": "(1, 0, 11) / 16", "launches": launches,
+                            "step_roofline_frac": pts * 12 / (ms * 1e-3) / (peak * 1e9), "peak_kind": kind,
+                            "kernels_ms": kern, "accuracy": sampled_accuracy(x, y, n, dev, skew=skew),
+                            "form": "r32: generic orbit mixing + register-radix DFT passes"}
+    del x, y
     return out
 
 

@@ -93,6 +93,32 @@ fcc_plan* fcc_dct_plan(int order, int batch, int dtype);
  */
 fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype);
 
+/*
+ * Plan for the skew transform DCT_{n x n x n}(r,s,t) of Def. 2 (its explicit
+ * matrix form, Sec. 4.A; the points are the common zeros of Lemma 2):
+ *
+ *   y[i,l,q] = sum_{j,k,p} x[j,k,p] T_{j,k,p}(((r+i)/n, (s+l)/n, (t+q)/n)),
+ *   (r, s, t) = (v[0], v[1], v[2]) / d,
+ *
+ * with 1 <= d <= FCC_MAX_SHIFT_DEN and |v[i]| <= FCC_MAX_SHIFT_NUM (`v` is a
+ * host array of 3 ints read during the call only).  (1/8, 0, 3/8), in any
+ * form such as (2, 0, 6) / 16, is the plan of fcc_dct_plan.  Same layouts,
+ * entry points and errors otherwise, with these differences for any other
+ * shift:
+ *   - dtypes FCC_R64, FCC_C64, FCC_R32, FCC_C32 only (the tensor-core dtypes
+ *     return NULL with FCC_ERR_UNSUPPORTED: their exact core split needs the
+ *     8th-root cores of the shift (1/8, 0, 3/8));
+ *   - D is invertible only when every W-orbit block is; this holds for the
+ *     shifts (c + a)/2 (a in {0,1}^3) of the radix-2 step of Sec. 4.B, c =
+ *     (1/8, 0, 3/8), and fails for most others (e.g. (0,0,0), (1,1,1)/4).
+ *     For a singular D the plan is still built (forward and adjoint work)
+ *     and fcc_dct_inverse / fcc_dct_inverse_host return FCC_ERR_UNSUPPORTED;
+ *   - fcc_dct_inverse_static returns FCC_ERR_UNSUPPORTED.
+ */
+#define FCC_MAX_SHIFT_DEN 1024
+#define FCC_MAX_SHIFT_NUM 65536
+fcc_plan* fcc_dct_plan_skew(int order, int batch, int dtype, const int* v, int d);
+
 /* y = D x over the plan's batch; in: coefficients, out: point values. */
 fcc_status fcc_dct_forward(fcc_plan* plan, const void* in, void* out, void* stream);
 
@@ -256,6 +282,13 @@ void fcc_dct_destroy(fcc_plan* plan);
 fcc_status fcc_dct_describe(int order, int64_t* n_orbits, int* n_classes, int* free_class,
                             uint32_t* reps, int32_t* cls, int32_t* wrap, int32_t* canon,
                             double* fwd, double* inv, double* adj);
+
+/* The same for the skew transform of shift v / d (as fcc_dct_plan_skew);
+ * *invertible (if non-NULL) is 1 when every class block is invertible, else
+ * 0 (the inverse core of each singular class is then left zero). */
+fcc_status fcc_dct_describe_skew(int order, const int* v, int d, int* invertible, int64_t* n_orbits,
+                                 int* n_classes, int* free_class, uint32_t* reps, int32_t* cls, int32_t* wrap,
+                                 int32_t* canon, double* fwd, double* inv, double* adj);
 
 /* The 24 group matrices (row-major 3x3 each) the library uses. */
 fcc_status fcc_dct_weyl_group(int32_t* out /* 216 */);

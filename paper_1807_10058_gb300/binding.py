@@ -22,6 +22,7 @@ EXPORTS = [
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
     "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
     "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune", "fcc_dct_test_wait_timeout",
+    "fcc_dct_plan_skew", "fcc_dct_describe_skew",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -48,6 +49,11 @@ def lib():
         L.fcc_dct_plan.restype = vp
         L.fcc_dct_plan_ragged.argtypes = [ctypes.POINTER(i32), i32, i32]
         L.fcc_dct_plan_ragged.restype = vp
+        L.fcc_dct_plan_skew.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
+        L.fcc_dct_plan_skew.restype = vp
+        L.fcc_dct_describe_skew.argtypes = [i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i32), ctypes.POINTER(i32)] + [vp] * 7
+        L.fcc_dct_describe_skew.restype = i32
         for f in ("fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint", "fcc_dct_forward_host",
                   "fcc_dct_inverse_host", "fcc_dct_inverse_static"):
             getattr(L, f).argtypes = [vp, vp, vp, vp]
@@ -101,25 +107,30 @@ def _check(status, what):
         raise FccError(status, what)
 
 
-def describe(order):
-    """Host-side orbit tables of the plan builder (no GPU needed)."""
+def describe(order, skew=None):
+    """Host-side orbit tables of the plan builder (no GPU needed).  skew:
+    ((v0, v1, v2), d) for the shift v / d of DCT_n(r,s,t), None for (1/8, 0, 3/8)."""
     L = lib()
+    v, d = skew if skew is not None else ((1, 0, 3), 8)
+    varr = (ctypes.c_int * 3)(*[int(a) for a in v])
+    inv_ok = ctypes.c_int()
     no, nc, fc = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
-    _check(L.fcc_dct_describe(order, ctypes.byref(no), ctypes.byref(nc), ctypes.byref(fc),
-                              None, None, None, None, None, None, None), "describe")
+    _check(L.fcc_dct_describe_skew(order, varr, int(d), ctypes.byref(inv_ok), ctypes.byref(no), ctypes.byref(nc),
+                                   ctypes.byref(fc), None, None, None, None, None, None, None), "describe")
     reps = np.zeros(no.value, dtype=np.uint32)
     cls = np.zeros(no.value, dtype=np.int32)
     wrap = np.zeros(nc.value * 72, dtype=np.int32)
     canon = np.zeros(nc.value * 24, dtype=np.int32)
     mats = [np.zeros(nc.value * 576 * 2) for _ in range(3)]
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    _check(L.fcc_dct_describe(order, ctypes.byref(no), ctypes.byref(nc), ctypes.byref(fc), ptr(reps),
-                              ptr(cls), ptr(wrap), ptr(canon), ptr(mats[0]), ptr(mats[1]), ptr(mats[2])),
-           "describe")
+    _check(L.fcc_dct_describe_skew(order, varr, int(d), ctypes.byref(inv_ok), ctypes.byref(no), ctypes.byref(nc),
+                                   ctypes.byref(fc), ptr(reps), ptr(cls), ptr(wrap), ptr(canon), ptr(mats[0]),
+                                   ptr(mats[1]), ptr(mats[2])), "describe")
     cx = [(m[0::2] + 1j * m[1::2]).reshape(nc.value, 24, 24) for m in mats]
     k = np.stack([reps & 1023, (reps >> 10) & 1023, (reps >> 20) & 1023], 1).astype(np.int64)
     return {"reps": k, "cls": cls, "free_class": fc.value, "wrap": wrap.reshape(-1, 24, 3),
-            "canon": canon.reshape(-1, 24), "fwd": cx[0], "inv": cx[1], "adj": cx[2]}
+            "canon": canon.reshape(-1, 24), "fwd": cx[0], "inv": cx[1], "adj": cx[2],
+            "invertible": bool(inv_ok.value)}
 
 
 def weyl_group():
@@ -133,9 +144,11 @@ _REAL_T = {0: "float64", 1: "float64", 2: "float32", 3: "float32", 4: "float32",
 
 class Plan:
     """A device plan for `batch` volumes of order `order` (or a ragged list of
-    orders).  Owns the library handle; release with close() or `with`."""
+    orders).  skew = ((v0, v1, v2), d): the skew transform DCT_n(r,s,t) with
+    (r, s, t) = v / d (uniform batches).  Owns the library handle; release
+    with close() or `with`."""
 
-    def __init__(self, order=None, batch=1, dtype="r32", orders=None):
+    def __init__(self, order=None, batch=1, dtype="r32", orders=None, skew=None):
         import torch  # noqa: F401  (initialises the CUDA context torch uses)
         L = lib()
         self.dtype_code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -143,6 +156,11 @@ class Plan:
             arr = (ctypes.c_int * len(orders))(*[int(o) for o in orders])
             h = L.fcc_dct_plan_ragged(arr, len(orders), self.dtype_code)
             self.orders = [int(o) for o in orders]
+        elif skew is not None:
+            v, d = skew
+            varr = (ctypes.c_int * 3)(*[int(a) for a in v])
+            h = L.fcc_dct_plan_skew(int(order), int(batch), self.dtype_code, varr, int(d))
+            self.orders = [int(order)] * int(batch)
         else:
             h = L.fcc_dct_plan(int(order), int(batch), self.dtype_code)
             self.orders = [int(order)] * int(batch)

@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <numeric>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -55,7 +56,9 @@ struct OrderTables {
     int8_t* wrap = nullptr;
     uint32_t* canon_mask = nullptr;
     void* mat[3] = {nullptr, nullptr, nullptr};  // fwd, inv, adj
-    void* phase = nullptr;                        // [8n] complex
+    void* phase = nullptr;                        // [M] complex, exp(2 pi i e / M), M = d n
+    int u[24][3] = {};                            // W_h^T v for the shift c = v / d
+    int M = 0;
     void* tw = nullptr;                           // [n] complex, exp(+2 pi i j / n)
     // tiled mixing (FP32 plans)
     int free_class = -1;
@@ -92,6 +95,11 @@ struct fcc_plan {
     int dtype = 0;
     int batch = 0;
     bool uniform = true;
+    // shift c = v / d of DCT_n(r,s,t); skew: any shift other than (1/8, 0, 3/8)
+    int shift_v[3] = {1, 0, 3};
+    int shift_d = 8;
+    bool skew = false;
+    bool invertible = true;          // every class block of every order invertible
     std::vector<int> orders;         // per volume
     std::vector<int64_t> offset;     // point offset of each volume
     int64_t points = 0;
@@ -167,10 +175,16 @@ fcc_status upload(fcc_plan* p, void** ptr, const void* src, size_t bytes) {
 template <typename T>
 fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     HostPlan hp;
-    const int rc = build_host_plan(n, hp);
+    const int rc = build_host_plan(n, hp, p->shift_v, p->shift_d);
     if (rc == -1) return FCC_ERR_INVALID_ARG;
     if (rc != 0) return FCC_ERR_UNSUPPORTED;
+    if (!hp.invertible) {
+        if (!p->skew) return FCC_ERR_UNSUPPORTED;   // the canonical blocks are never singular
+        p->invertible = false;
+    }
     t.n = n;
+    t.M = hp.d * n;
+    std::memcpy(t.u, hp.u, sizeof(t.u));
     t.n_orbits = (int64_t)hp.reps.size();
     t.n_classes = (int)hp.classes.size();
     t.radices = fft_radices(n);
@@ -188,8 +202,8 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
         mats[1].insert(mats[1].end(), oc.inv.begin(), oc.inv.end());
         mats[2].insert(mats[2].end(), oc.adj.begin(), oc.adj.end());
     }
-    std::vector<cd> phase(8 * n), tw(n);
-    for (int e = 0; e < 8 * n; ++e) phase[e] = std::polar(1.0, 2.0 * M_PI * e / (8.0 * n));
+    std::vector<cd> phase(t.M), tw(n);
+    for (int e = 0; e < t.M; ++e) phase[e] = std::polar(1.0, 2.0 * M_PI * e / (double)t.M);
     for (int j = 0; j < n; ++j) tw[j] = std::polar(1.0, 2.0 * M_PI * j / (double)n);
     fcc_status s;
     if ((s = upload(p, (void**)&t.reps, hp.reps.data(), hp.reps.size() * 4))) return s;
@@ -260,8 +274,9 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
             for (int i = 0; i < 3; ++i)
                 if (hp.classes[hp.free_class].wrap[g][i] != wc::K::t.fw[g][i]) return FCC_ERR_UNSUPPORTED;
     }
-    if (sizeof(T) == 4 && hp.free_class >= 0) {
+    if (sizeof(T) == 4 && hp.free_class >= 0 && !p->skew) {
         // the free-orbit cores do not depend on n: one constant copy per device
+        // (for the canonical shift; skew plans mix with the generic kernel)
         std::vector<float2> core(3 * 576);
         const OrbitClass& oc = hp.classes[hp.free_class];
         for (int e = 0; e < 576; ++e) {
@@ -317,7 +332,15 @@ void release(fcc_plan* p) {
     delete p;
 }
 
-fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
+// c = v / d in lowest terms is (1/8, 0, 3/8): the canonical kernels apply
+bool canonical_shift(const int* v, int d) {
+    int g = d;
+    for (int i = 0; i < 3; ++i) g = std::gcd(g, std::abs(v[i]));
+    return v[0] / g == 1 && v[1] == 0 && v[2] / g == 3 && d / g == 8;
+}
+
+// v, d: the shift c = v / d (v = nullptr: (1/8, 0, 3/8)).
+fcc_plan* make_plan(const std::vector<int>& orders, int dtype, const int* v = nullptr, int d = 8) {
     if (dtype < FCC_R64 || dtype > FCC_R32_BF16X6) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     if (orders.empty()) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     for (int n : orders)
@@ -326,6 +349,11 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype) {
     if (!p) { fail(FCC_ERR_ALLOC); return nullptr; }
     if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); delete p; fail(FCC_ERR_CUDA); return nullptr; }
     p->dtype = dtype;
+    if (v && !canonical_shift(v, d)) {   // (1/8, 0, 3/8) in other terms keeps the canonical tables
+        for (int i = 0; i < 3; ++i) p->shift_v[i] = v[i];
+        p->shift_d = d;
+        p->skew = true;
+    }
     p->batch = (int)orders.size();
     p->orders = orders;
     p->uniform = std::all_of(orders.begin(), orders.end(), [&](int n) { return n == orders[0]; });
@@ -489,6 +517,8 @@ fcc_status launch_mix(const OrderTables& t, int mode, bool real_in, bool real_ou
     a.wrap = t.wrap;
     a.canon_mask = t.canon_mask;
     a.phase = (const T*)t.phase;
+    std::memcpy(a.u, t.u, sizeof(a.u));
+    a.M = t.M;
     a.n = t.n;
     a.n_orbits = t.n_orbits;
     a.n3 = (int64_t)t.n * t.n * t.n;
@@ -936,10 +966,47 @@ fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_
     return s;
 }
 
+// Skew plans, FP32: the generic per-orbit mixing (row-phase weights and
+// modulus of the plan's shift) and the register-radix DFT passes where the
+// order has them; chunks of volumes in sequence on the caller's stream, so
+// that each chunk's intermediate stays in L2 between its passes.  Real volumes
+// are not paired: the conjugate-point involution the pairing relies on
+// belongs to the shift (1/8, 0, 3/8).
+fcc_status run_group_skew(fcc_plan* p, int which, const OrderTables& t, const float* in, float* out, int64_t nvol,
+                          cudaStream_t st) {
+    const bool rin = is_real_in(p->dtype);
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    fcc_status s = FCC_OK;
+    if (which == 0) {
+        const int64_t cv = chunk_vols(p, t.n);
+        const int64_t in_stride = (rin ? 1 : 2) * n3;
+        for (int64_t v0 = 0; v0 < nvol && !s; v0 += cv) {
+            const int64_t nv = std::min(cv, nvol - v0);
+            float* y = out + v0 * 2 * n3;
+            s = launch_mix<float>(t, MODE_FWD, rin, false, in + v0 * in_stride, y, nv, 1.f, st);
+            if (!s) s = launch_dft3(t, +1, y, y, nv, st);
+        }
+        return s;
+    }
+    const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
+    const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
+    const int64_t out_stride = (rin ? 1 : 2) * n3;
+    float* ws = (float*)p->scratch;
+    for (int64_t v0 = 0; v0 < nvol && !s; v0 += chunk) {
+        const int64_t nv = std::min(chunk, nvol - v0);
+        s = launch_dft3(t, -1, in + v0 * 2 * n3, ws, nv, st);
+        if (!s) s = launch_mix<float>(t, which == 1 ? MODE_INV : MODE_ADJ, false, rin, ws, out + v0 * out_stride, nv,
+                                      scale, st);
+    }
+    return s;
+}
+
 // Run a group of `nvol` consecutive volumes of the same order.
 template <typename T>
 fcc_status run_group(fcc_plan* p, int which, const OrderTables& t, const T* in, T* out, int64_t nvol,
                      cudaStream_t st) {
+    if (sizeof(T) == 4 && t.n > 1 && p->skew)
+        return run_group_skew(p, which, t, (const float*)in, (float*)out, nvol, st);
     if (sizeof(T) == 4 && t.n > 1)
         return run_group_fast(p, which, t, (const float*)in, (float*)out, nvol, st);
     const bool rin = is_real_in(p->dtype);
@@ -1012,6 +1079,7 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
         *(volatile int*)p->h_status = 0;
         return fail(FCC_ERR_TIMEOUT);
     }
+    if (which == 1 && !p->invertible) return fail(FCC_ERR_UNSUPPORTED);
     if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, which);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, which);
@@ -1069,6 +1137,7 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
 
 fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream) {
     if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
+    if (which == 1 && !p->invertible) return fail(FCC_ERR_UNSUPPORTED);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t ib = in_bytes(p, which), ob = out_bytes(p, which);
     const int64_t cap = std::max(in_bytes(p, 0), in_bytes(p, 1));
@@ -1100,6 +1169,22 @@ extern "C" {
 fcc_plan* fcc_dct_plan(int order, int batch, int dtype) {
     if (batch < 1 || order < 1 || order > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     return make_plan(std::vector<int>((size_t)batch, order), dtype);
+}
+
+static_assert(FCC_MAX_SHIFT_DEN == kMaxShiftDen && FCC_MAX_SHIFT_NUM == kMaxShiftNum, "shift limits");
+
+fcc_plan* fcc_dct_plan_skew(int order, int batch, int dtype, const int* v, int d) {
+    if (batch < 1 || order < 1 || order > FCC_MAX_ORDER || !v || d < 1 || d > FCC_MAX_SHIFT_DEN) {
+        fail(FCC_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    for (int i = 0; i < 3; ++i)
+        if (v[i] < -FCC_MAX_SHIFT_NUM || v[i] > FCC_MAX_SHIFT_NUM) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    if (dtype < FCC_R64 || dtype > FCC_R32_BF16X6) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    // the tensor-core forms rely on the exact split of 8th-root cores and on
+    // the canonical row phases
+    if (is_tc(dtype) && !canonical_shift(v, d)) { fail(FCC_ERR_UNSUPPORTED); return nullptr; }
+    return make_plan(std::vector<int>((size_t)batch, order), dtype, v, d);
 }
 
 fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype) {
@@ -1254,7 +1339,13 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         const int64_t n3 = (int64_t)n * n * n;
         const int64_t nv = e - v;
         const int mix = (int)((nv + 65534) / 65535);
-        if (!is_double(p->dtype) && n > 1) {
+        if (!is_double(p->dtype) && n > 1 && p->skew) {
+            // run_group_skew: per chunk the mixing launches and the DFT passes
+            const int dft = has_fast_fft(n) ? 2 : 3;
+            const int64_t cv = which == 0 ? chunk_vols(p, n) : std::max<int64_t>(1, p->scratch_points / n3);
+            for (int64_t v0 = 0; v0 < nv; v0 += cv)
+                total += (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
+        } else if (!is_double(p->dtype) && n > 1) {
             const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
             const int dft = has_fast_fft(n) ? 2 : 3;
             const OrderTables& tb = p->tabs.at(n);
@@ -1364,10 +1455,20 @@ void fcc_dct_destroy(fcc_plan* p) { release(p); }
 fcc_status fcc_dct_describe(int order, int64_t* n_orbits, int* n_classes, int* free_class, uint32_t* reps,
                             int32_t* cls, int32_t* wrap, int32_t* canon, double* fwd, double* inv,
                             double* adj) {
+    static const int v0[3] = {1, 0, 3};
+    return fcc_dct_describe_skew(order, v0, 8, nullptr, n_orbits, n_classes, free_class, reps, cls, wrap, canon, fwd,
+                                 inv, adj);
+}
+
+fcc_status fcc_dct_describe_skew(int order, const int* v, int d, int* invertible, int64_t* n_orbits, int* n_classes,
+                                 int* free_class, uint32_t* reps, int32_t* cls, int32_t* wrap, int32_t* canon,
+                                 double* fwd, double* inv, double* adj) {
+    if (!v) return fail(FCC_ERR_INVALID_ARG);
     HostPlan hp;
-    const int rc = build_host_plan(order, hp);
+    const int rc = build_host_plan(order, hp, v, d);
     if (rc == -1) return fail(FCC_ERR_INVALID_ARG);
     if (rc != 0) return fail(FCC_ERR_UNSUPPORTED);
+    if (invertible) *invertible = hp.invertible ? 1 : 0;
     if (n_orbits) *n_orbits = (int64_t)hp.reps.size();
     if (n_classes) *n_classes = (int)hp.classes.size();
     if (free_class) *free_class = hp.free_class;
@@ -1482,7 +1583,7 @@ extern "C" fcc_status fcc_dct_inverse_static(fcc_plan* p, const void* in, void* 
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, 1);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, 1);
     if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
-    if (p->dtype != FCC_R32 && p->dtype != FCC_C32) return fail(FCC_ERR_UNSUPPORTED);
+    if ((p->dtype != FCC_R32 && p->dtype != FCC_C32) || p->skew) return fail(FCC_ERR_UNSUPPORTED);
     for (int n : p->orders)
         if ((uint64_t)n * n * n * sizeof(float2) > FCC_STATIC_SCRATCH_BYTES) return fail(FCC_ERR_UNSUPPORTED);
     int cur = 0;

@@ -27,7 +27,9 @@ struct MixArgs {
     const T* mats;              // [n_classes][24][24][2] (re, im) for this mode
     const int8_t* wrap;         // [n_classes][24][3]
     const uint32_t* canon_mask; // [n_classes]
-    const T* phase;             // [8n][2]: exp(2 pi i e / (8n))
+    const T* phase;             // [M][2]: exp(2 pi i e / M), M = d n for the shift c = v / d
+    int u[24][3];               // W_h^T v: the row-phase exponent of slot h is u_h . kO mod M
+    int M;
     int n;
     int64_t n_orbits;
     int64_t n3;                 // points per volume
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(128) orbit_mix_kernel(const T* __restrict__ in
     const uint32_t cm = a.canon_mask[c];
     const T* M = a.mats + (size_t)c * 1152;
     const int n = a.n;
-    const int M8 = 8 * n;
+    const int PM = a.M;   // phase-table length d n
     int idx[24];
     int ph[24];
 #pragma unroll
@@ -58,8 +60,8 @@ __global__ void __launch_bounds__(128) orbit_mix_kernel(const T* __restrict__ in
         const int p1 = c_W[h][3] * k0 + c_W[h][4] * k1 + c_W[h][5] * k2 - n * wr[3 * h + 1];
         const int p2 = c_W[h][6] * k0 + c_W[h][7] * k1 + c_W[h][8] * k2 - n * wr[3 * h + 2];
         idx[h] = (p0 * n + p1) * n + p2;
-        int e = (c_u[h][0] * k0 + c_u[h][1] * k1 + c_u[h][2] * k2) % M8;
-        ph[h] = e < 0 ? e + M8 : e;
+        int e = (a.u[h][0] * k0 + a.u[h][1] * k1 + a.u[h][2] * k2) % PM;
+        ph[h] = e < 0 ? e + PM : e;
     }
     if (MODE == MODE_FWD) {
         const T* src = in + vol * a.n3 * (RIN ? 1 : 2);

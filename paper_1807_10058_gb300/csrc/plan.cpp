@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <numeric>
 
 namespace fcc {
 
@@ -65,6 +66,18 @@ WeylGroup make_weyl() {
 }
 
 // exact 8th roots of unity w_8^e
+cd root8(int e);
+
+// w_d^e: exact when e / d in lowest terms has a denominator dividing 8,
+// else from the reduced angle
+cd root_d(int64_t e, int d) {
+    e = ((e % d) + d) % d;
+    const int64_t g = std::gcd(e, (int64_t)d);
+    const int64_t dr = d / g;
+    if (8 % dr == 0) return root8((int)((e / g) * (8 / dr)));
+    return std::polar(1.0, 2.0 * M_PI * (double)e / (double)d);
+}
+
 cd root8(int e) {
     e = ((e % 8) + 8) % 8;
     const double h = std::sqrt(0.5);
@@ -128,11 +141,23 @@ std::vector<int> fft_radices(int n) {
     return r;
 }
 
-int build_host_plan(int n, HostPlan& P) {
+int build_host_plan(int n, HostPlan& P, const int* v, int d) {
     if (n < 1 || n > kMaxOrder) return -1;
+    if (!v) { v = kV; d = 8; }
+    if (d < 1 || d > kMaxShiftDen) return -1;
+    for (int i = 0; i < 3; ++i)
+        if (v[i] < -kMaxShiftNum || v[i] > kMaxShiftNum) return -1;
     const WeylGroup& G = weyl();
     P = HostPlan();
     P.n = n;
+    P.d = d;
+    for (int i = 0; i < 3; ++i) P.v[i] = v[i];
+    for (int g = 0; g < 24; ++g)
+        for (int j = 0; j < 3; ++j) {
+            int acc = 0;
+            for (int i = 0; i < 3; ++i) acc += G.m[g][3 * i + j] * v[i];
+            P.u[g][j] = acc;
+        }
     P.points = (int64_t)n * n * n;
     std::vector<uint8_t> seen(P.points, 0);
     std::map<ClassKey, int> key2cls;
@@ -207,13 +232,13 @@ int build_host_plan(int n, HostPlan& P) {
         for (int g = 0; g < 24; ++g)
             for (int h = 0; h < 24; ++h) {
                 const int w = G.mul[g][G.inv[h]];
-                int t = 0;
+                int64_t t = 0;
                 for (int i = 0; i < 3; ++i) {
                     const int wm = G.m[w][3 * i] * oc.wrap[h][0] + G.m[w][3 * i + 1] * oc.wrap[h][1] +
                                    G.m[w][3 * i + 2] * oc.wrap[h][2];
-                    t += wm * kV[i];
+                    t += (int64_t)wm * v[i];
                 }
-                oc.fwd[g * 24 + h] = root8(-t) / 24.0;
+                oc.fwd[g * 24 + h] = root_d(-t, d) / 24.0;
             }
         // distinct-member block B (s x s): rows at canonical slots, columns
         // summed over slots holding the same member
@@ -223,13 +248,14 @@ int build_host_plan(int n, HostPlan& P) {
             for (int h = 0; h < 24; ++h) B[oc.dist[g] * s + oc.dist[h]] += oc.fwd[g * 24 + h];
         }
         std::vector<cd> Binv = B;
-        if (!invert(Binv, s)) return -2;
+        const bool inv_ok = invert(Binv, s);
+        P.invertible = P.invertible && inv_ok;
         oc.inv.assign(576, cd(0));
         oc.adj.assign(576, cd(0));
         for (int h = 0; h < 24; ++h)
             for (int g = 0; g < 24; ++g) {
                 if (oc.canon[g] != g) continue;
-                oc.inv[h * 24 + g] = Binv[oc.dist[h] * s + oc.dist[g]];
+                if (inv_ok) oc.inv[h * 24 + g] = Binv[oc.dist[h] * s + oc.dist[g]];
                 oc.adj[h * 24 + g] = std::conj(B[oc.dist[g] * s + oc.dist[h]]);
             }
     }

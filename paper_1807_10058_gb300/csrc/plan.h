@@ -1,6 +1,7 @@
 // Host-side plan builder for the FCC cosine transform (no CUDA code here).
 //
-// The transform of Def. 2 (explicit matrix form, Sec. 4.A) factors exactly as
+// The skew transform DCT_n(r,s,t) of Def. 2 (explicit matrix form, Sec. 4.A)
+// factors exactly as
 //
 //   y = DCT_n x = F S x,
 //
@@ -8,11 +9,11 @@
 // block diagonal over the W-orbits of Z_n^3 (W = the group of Sec. 3
 // generated by s1, s2, s3, acting on the coefficient index k from the left as
 // in the power form).  This follows from the power form of T_k evaluated at
-// theta = (c + idx)/n with c = (1/8, 0, 3/8):
+// theta = (c + idx)/n, c = (r, s, t) = v / d with v integer (the FCC cosine
+// transform proper: v = (1, 0, 3), d = 8):
 //
 //   y[idx] = sum_kappa Z[kappa] w_n^{kappa.idx},
-//   Z[kappa] = (1/24) sum_{(k,w): w k = kappa mod n} x_k w_{8n}^{(w k).v},
-//   v = 8c = (1, 0, 3).
+//   Z[kappa] = (1/24) sum_{(k,w): w k = kappa mod n} x_k w_{dn}^{(w k).v}.
 //
 // Each orbit O is described by an integer representative kO in the closed
 // alcove {k >= 0, k1+k2+k3 <= n} and 24 "slots" h (one per group element):
@@ -20,11 +21,14 @@
 // Then, for every slot g,
 //
 //   Z[kappa_g] = R_g * sum_h E[g][h] x[kappa_h] / 24,
-//   R_g = w_{8n}^{p_g.v},   E[g][h] = w_8^{-(W_g W_h^{-1} m_h).v}.
+//   R_g = w_{dn}^{p_g.v},   E[g][h] = w_d^{-(W_g W_h^{-1} m_h).v}.
 //
 // E depends only on the wrap vectors and on which slots coincide, so orbits
 // fall into a handful of classes; all free orbits (95% of the points at
-// n = 128) share one class whose core has 8th roots of unity as entries.
+// n = 128) share one class.  For d = 8 every core has 8th roots of unity as
+// entries.  D = F S is invertible exactly when every class block is (F is);
+// for most shifts other than (1/8, 0, 3/8) and the halved shifts of the
+// radix-2 recursion, some block is singular.
 #pragma once
 #include <array>
 #include <complex>
@@ -58,6 +62,10 @@ struct OrbitClass {
 
 struct HostPlan {
     int n = 0;
+    int v[3] = {1, 0, 3};           // shift c = v / d
+    int d = 8;
+    int u[24][3] = {};              // W_g^T v: (W_g k).v = u_g . k
+    bool invertible = true;         // every class block invertible (else inv cores are zero)
     int64_t points = 0;             // n^3
     std::vector<uint32_t> reps;     // packed representative: k1 | k2 << 10 | k3 << 20
     std::vector<uint8_t> cls;       // class of each orbit
@@ -95,9 +103,13 @@ void slot_directions(int dir[24]);
 // Orders supported by the packing of representatives.
 constexpr int kMaxOrder = 512;
 
-// Returns 0 on success, -1 on invalid order, -2 on an internal consistency
-// failure (a member not covered exactly once, a singular class block).
-int build_host_plan(int n, HostPlan& out);
+// Returns 0 on success, -1 on invalid order or shift, -2 on an internal
+// consistency failure (a member not covered exactly once).  v, d: the shift
+// c = v / d (1 <= d <= kMaxShiftDen, |v_i| <= kMaxShiftNum); v = nullptr
+// selects (1/8, 0, 3/8).  A singular class block clears `invertible`.
+constexpr int kMaxShiftDen = 1024;
+constexpr int kMaxShiftNum = 1 << 16;
+int build_host_plan(int n, HostPlan& out, const int* v = nullptr, int d = 8);
 
 // Factorisation of a DFT length into the radices the kernels implement.
 std::vector<int> fft_radices(int n);

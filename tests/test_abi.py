@@ -47,6 +47,23 @@ def test_invalid_ragged_arguments():
     assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("v,d,dtype,status", [
+    ((1, 0, 3), 0, 2, binding.FCC_ERR_INVALID_ARG),          # d < 1
+    ((1, 0, 3), 1025, 2, binding.FCC_ERR_INVALID_ARG),       # d > FCC_MAX_SHIFT_DEN
+    ((1, 70000, 3), 8, 2, binding.FCC_ERR_INVALID_ARG),      # |v| > FCC_MAX_SHIFT_NUM
+    ((1, 0, 11), 16, 9, binding.FCC_ERR_INVALID_ARG),        # dtype
+    ((1, 0, 11), 16, 5, binding.FCC_ERR_UNSUPPORTED),        # tensor-core dtype, other shift
+    ((9, 0, 3), 8, 4, binding.FCC_ERR_UNSUPPORTED),
+])
+def test_invalid_skew_plan_arguments(v, d, dtype, status):
+    L = binding.lib()
+    arr = (ctypes.c_int * 3)(*v)
+    assert not L.fcc_dct_plan_skew(8, 2, dtype, arr, d)
+    assert L.fcc_dct_last_error() == status
+    assert not L.fcc_dct_plan_skew(8, 2, 2, None, 8)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
+
+
 def test_null_plan_calls():
     L = binding.lib()
     for f in (L.fcc_dct_forward, L.fcc_dct_inverse, L.fcc_dct_adjoint, L.fcc_dct_forward_host,

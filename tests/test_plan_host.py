@@ -13,13 +13,14 @@ import pytest
 import oracle
 from paper_1807_10058_gb300 import binding
 
-V = np.array([1, 0, 3])
 RNG = np.random.default_rng(5)
+CANONICAL = ((1, 0, 3), 8)
 
 
-def _tables(n):
-    d = binding.describe(n)
+def _tables(n, skew=CANONICAL):
+    d = binding.describe(n, skew)
     d["W"] = binding.weyl_group()
+    d["v"], d["d"] = np.array(skew[0]), skew[1]
     return d
 
 
@@ -30,7 +31,8 @@ def _slots(d, n, o):
     kap = p - n * d["wrap"][c]
     assert kap.min() >= 0 and kap.max() < n
     idx = (kap[:, 0] * n + kap[:, 1]) * n + kap[:, 2]
-    R = np.exp(2j * np.pi * np.mod(p @ V, 8 * n) / (8 * n))
+    M = d["d"] * n
+    R = np.exp(2j * np.pi * np.mod(p @ d["v"], M) / M)
     canon = d["canon"][c] == np.arange(24)
     return c, idx, R, canon
 
@@ -110,3 +112,39 @@ def test_emulated_forward_order_24_sampled_rows():
     y = emulate(d, n, x, "fwd").reshape(-1)
     rows = RNG.integers(0, n ** 3, size=12)
     assert np.abs(y[rows] - oracle.forward_rows(x, n, rows)).max() < 1e-10
+
+
+# shifts of DCT_n(r,s,t): the halved shifts (c + a)/2 of the radix-2 step
+# (invertible), c + e1 (the canonical points moved by one grid step), a shift
+# with a denominator that is not a power of two, and two singular ones
+SKEWS = [((1, 0, 11), 16), ((9, 8, 11), 16), ((1, 0, 3), 32), ((9, 0, 3), 8), ((5, 3, 1), 24), ((0, 0, 0), 1),
+         ((1, 1, 1), 4)]
+
+
+@pytest.mark.parametrize("skew", SKEWS)
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+def test_emulated_skew_transforms_match_oracle(n, skew):
+    d = _tables(n, skew)
+    D = oracle.dct_matrix(n, skew)
+    sv = np.linalg.svd(D, compute_uv=False)
+    # the plan's block test agrees with the rank of the dense matrix
+    assert d["invertible"] == (sv[-1] > 1e-9 * sv[0])
+    x = RNG.standard_normal((n, n, n)) + 1j * RNG.standard_normal((n, n, n))
+    y = (D @ x.reshape(-1)).reshape(n, n, n)
+    tol = 1e-11 * max(1, n ** 1.5)
+    assert np.abs(emulate(d, n, x, "fwd") - y).max() < tol
+    g = RNG.standard_normal((n, n, n)) + 1j * RNG.standard_normal((n, n, n))
+    ah = (D.conj().T @ g.reshape(-1)).reshape(n, n, n)
+    assert np.abs(emulate(d, n, g, "adj") - ah).max() < tol
+    if d["invertible"]:
+        assert np.abs(emulate(d, n, y, "inv") - x).max() < tol * sv[0] / sv[-1]
+    else:   # some class block is singular: its inverse core is left zero
+        assert any(not np.any(m) for m in d["inv"])
+
+
+def test_equal_shifts_give_equal_cores():
+    a = binding.describe(12, CANONICAL)
+    b = binding.describe(12, ((2, 0, 6), 16))
+    assert np.array_equal(a["reps"], b["reps"]) and np.array_equal(a["cls"], b["cls"])
+    for m in ("fwd", "inv", "adj"):
+        assert np.abs(a[m] - b[m]).max() < 1e-15
