@@ -325,8 +325,9 @@ def secondary_configs(dev):
     out["autograd_gd_n96_b32"] = {"ms_per_gd_step": ms_gd, "steps_timed": 50, "loss_ratio_after": final / l0,
                                   "note": "forward + adjoint backward per step, step size 1e-6"}
     # the skew transform DCT_n(1/16, 0, 11/16) of Def. 2 (a halved shift of the
-    # radix-2 step), order 128 x 64, FP32: generic orbit mixing with the
-    # plan's row phases + the register-radix DFT passes, no pairing
+    # radix-2 step), order 128 x 64, FP32: tiled orbit mixing on the staged
+    # class cores with the plan's row phases + the register-radix DFT passes,
+    # no pairing
     n, b, skew = 128, 64, ((1, 0, 11), 16)
     x = inputs.phantom_device(n, b, seed=5, device=dev)
     y = torch.empty(b * n ** 3, dtype=torch.complex64, device=dev)
@@ -344,7 +345,7 @@ def secondary_configs(dev):
                             "shift": "(1, 0, 11) / 16", "launches": launches,
                             "step_roofline_frac": pts * 12 / (ms * 1e-3) / (peak * 1e9), "peak_kind": kind,
                             "kernels_ms": kern, "accuracy": sampled_accuracy(x, y, n, dev, skew=skew),
-                            "form": "r32: generic orbit mixing + register-radix DFT passes"}
+                            "form": "r32: tiled orbit mixing on staged class cores + register-radix DFT passes"}
     del x, y
     return out
 

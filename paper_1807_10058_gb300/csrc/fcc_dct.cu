@@ -58,7 +58,9 @@ struct OrderTables {
     void* mat[3] = {nullptr, nullptr, nullptr};  // fwd, inv, adj
     void* phase = nullptr;                        // [M] complex, exp(2 pi i e / M), M = d n
     int u[24][3] = {};                            // W_h^T v for the shift c = v / d
+    int* u_dev = nullptr;                         // the same on the device
     int M = 0;
+    std::vector<SkewCore> skew_core;              // skew FP32 plans: free-orbit core per mode + weights
     void* tw = nullptr;                           // [n] complex, exp(+2 pi i j / n)
     // tiled mixing (FP32 plans)
     int free_class = -1;
@@ -216,6 +218,7 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
     }
     auto ph = to_pairs<T>(phase);
     if ((s = upload(p, &t.phase, ph.data(), ph.size() * sizeof(T)))) return s;
+    if ((s = upload(p, (void**)&t.u_dev, &t.u[0][0], sizeof(t.u)))) return s;
     auto twv = to_pairs<T>(tw);
     if ((s = upload(p, &t.tw, twv.data(), twv.size() * sizeof(T)))) return s;
     t.free_class = hp.free_class;
@@ -273,6 +276,19 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
         for (int g = 0; g < 24; ++g)
             for (int i = 0; i < 3; ++i)
                 if (hp.classes[hp.free_class].wrap[g][i] != wc::K::t.fw[g][i]) return FCC_ERR_UNSUPPORTED;
+    }
+    if (sizeof(T) == 4 && p->skew) {
+        // the row-phase weights serve every orbit (the inverse / adjoint
+        // apply conj(R) to all slots); the core only the free orbits
+        t.skew_core.assign(3, SkewCore{});
+        for (int md = 0; md < 3; ++md) {
+            std::memcpy(t.skew_core[md].u, hp.u, sizeof(hp.u));
+            if (hp.free_class < 0) continue;
+            const OrbitClass& oc = hp.classes[hp.free_class];
+            const std::vector<cd>& m = md == 0 ? oc.fwd : md == 1 ? oc.inv : oc.adj;
+            for (int e = 0; e < 576; ++e)
+                t.skew_core[md].m[e / 24][e % 24] = make_float2((float)m[e].real(), (float)m[e].imag());
+        }
     }
     if (sizeof(T) == 4 && hp.free_class >= 0 && !p->skew) {
         // the free-orbit cores do not depend on n: one constant copy per device
@@ -584,6 +600,8 @@ TiledMixArgs make_mix_args(const OrderTables& t, int mode, float scale) {
     a.wrap = t.wrap;
     a.canon_mask = t.canon_mask;
     a.phase = (const float2*)t.phase;
+    a.uv = t.u_dev;
+    a.M = t.M;
     a.n = t.n;
     const int n = t.n;
     for (int g = 0; g < 24; ++g) {
@@ -966,37 +984,88 @@ fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_
     return s;
 }
 
-// Skew plans, FP32: the generic per-orbit mixing (row-phase weights and
-// modulus of the plan's shift) and the register-radix DFT passes where the
-// order has them; chunks of volumes in sequence on the caller's stream, so
-// that each chunk's intermediate stays in L2 between its passes.  Real volumes
-// are not paired: the conjugate-point involution the pairing relies on
-// belongs to the shift (1/8, 0, 3/8).
+// Orbit mixing of a skew plan: the tiled kernels (free tiles on the plan's
+// free core, boundary tiles on their staged class cores, the plan's row
+// phases), else the generic per-orbit kernel.
+bool skew_tiled(const OrderTables& t) { return t.n_classes <= kMaxClasses; }
+
+// part: 0 every tile, 1 free tiles only, 2 boundary tiles only (tiled form)
+fcc_status launch_mix_skew(const OrderTables& t, int mode, bool real_io, const float* in, float* out, int64_t nvol,
+                           float scale, cudaStream_t st, int part = 0) {
+    if (!skew_tiled(t))
+        return launch_mix<float>(t, mode, mode == MODE_FWD && real_io, mode != MODE_FWD && real_io, in, out, nvol, scale,
+                                 st);
+    static const char* names[2][3] = {{"mix_skew_fwd", "mix_skew_inv", "mix_skew_adj"},
+                                      {"mix_skew_bnd_fwd", "mix_skew_bnd_inv", "mix_skew_bnd_adj"}};
+    const TiledMixArgs a = make_mix_args(t, mode, scale);
+    if (t.skew_core.size() != 3) return FCC_ERR_UNSUPPORTED;   // built for every FP32 skew order
+    const SkewCore& sc = t.skew_core[mode];
+    const int ranges[2][2] = {{0, t.free_tiles}, {t.free_tiles, t.ntiles}};
+    for (int rg = 0; rg < 2; ++rg) {
+        if (ranges[rg][1] <= ranges[rg][0] || (part == 1 && rg == 1) || (part == 2 && rg == 0)) continue;
+        ProfScope ps(names[rg][mode], st);
+        if (launch_mix_tiled_skew(a, sc, mode, real_io, in, out, ranges[rg][0], ranges[rg][1], rg == 1, nvol, st) !=
+            cudaSuccess)
+            return FCC_ERR_CUDA;
+    }
+    return FCC_OK;
+}
+
+// Skew plans, FP32: the orbit mixing of launch_mix_skew and the
+// register-radix DFT passes where the order has them, chunks of volumes
+// round-robin over the internal streams (each chunk's intermediate stays in
+// L2 between its passes).  The forward mixes the boundary tiles of every
+// volume in one launch on a stream of its own, concurrent with the chunks'
+// free mixing; each chunk's DFT passes wait for it.  Real volumes are not
+// paired: the conjugate-point involution the pairing relies on belongs to
+// the shift (1/8, 0, 3/8).
 fcc_status run_group_skew(fcc_plan* p, int which, const OrderTables& t, const float* in, float* out, int64_t nvol,
                           cudaStream_t st) {
     const bool rin = is_real_in(p->dtype);
     const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    const int ns = which == 0 ? p->nstreams : std::min(p->nstreams, p->scratch_streams);
+    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
     fcc_status s = FCC_OK;
+    const bool split_boundary = which == 0 && skew_tiled(t) && t.free_tiles > 0 && t.ntiles > t.free_tiles;
+    if (split_boundary) {
+        if (cudaStreamWaitEvent(p->bnd_stream, p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+        s = launch_mix_skew(t, MODE_FWD, rin, in, out, nvol, 1.f, p->bnd_stream, 2);
+        if (!s && cudaEventRecord(p->bnd_ev, p->bnd_stream) != cudaSuccess) s = FCC_ERR_CUDA;
+    }
+    int c = 0;
     if (which == 0) {
         const int64_t cv = chunk_vols(p, t.n);
         const int64_t in_stride = (rin ? 1 : 2) * n3;
-        for (int64_t v0 = 0; v0 < nvol && !s; v0 += cv) {
+        for (int64_t v0 = 0; v0 < nvol && !s; v0 += cv, ++c) {
             const int64_t nv = std::min(cv, nvol - v0);
+            cudaStream_t ss = p->streams[c % ns];
             float* y = out + v0 * 2 * n3;
-            s = launch_mix<float>(t, MODE_FWD, rin, false, in + v0 * in_stride, y, nv, 1.f, st);
-            if (!s) s = launch_dft3(t, +1, y, y, nv, st);
+            s = launch_mix_skew(t, MODE_FWD, rin, in + v0 * in_stride, y, nv, 1.f, ss, split_boundary ? 1 : 0);
+            if (!s && split_boundary && cudaStreamWaitEvent(ss, p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
+            if (!s) s = launch_dft3(t, +1, y, y, nv, ss);
         }
-        return s;
+    } else {
+        // each stream its slice of the workspace
+        const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
+        const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
+        const int64_t out_stride = (rin ? 1 : 2) * n3;
+        for (int64_t v0 = 0; v0 < nvol && !s; v0 += chunk, ++c) {
+            const int64_t nv = std::min(chunk, nvol - v0);
+            cudaStream_t ss = p->streams[c % ns];
+            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            s = launch_dft3(t, -1, in + v0 * 2 * n3, ws, nv, ss);
+            if (!s) s = launch_mix_skew(t, which == 1 ? MODE_INV : MODE_ADJ, rin, ws, out + v0 * out_stride, nv, scale, ss);
+        }
     }
-    const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
-    const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
-    const int64_t out_stride = (rin ? 1 : 2) * n3;
-    float* ws = (float*)p->scratch;
-    for (int64_t v0 = 0; v0 < nvol && !s; v0 += chunk) {
-        const int64_t nv = std::min(chunk, nvol - v0);
-        s = launch_dft3(t, -1, in + v0 * 2 * n3, ws, nv, st);
-        if (!s) s = launch_mix<float>(t, which == 1 ? MODE_INV : MODE_ADJ, false, rin, ws, out + v0 * out_stride, nv,
-                                      scale, st);
+    for (int i = 0; i < ns; ++i) {
+        if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    if (split_boundary) {
+        if (cudaEventRecord(p->bnd_join, p->bnd_stream) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->bnd_join, 0) != cudaSuccess) return FCC_ERR_CUDA;
     }
     return s;
 }
@@ -1340,11 +1409,18 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         const int64_t nv = e - v;
         const int mix = (int)((nv + 65534) / 65535);
         if (!is_double(p->dtype) && n > 1 && p->skew) {
-            // run_group_skew: per chunk the mixing launches and the DFT passes
+            // run_group_skew: per chunk the mixing launches (free and boundary
+            // tiles, or the generic kernel) and the DFT passes; the forward
+            // mixes the boundary tiles of every volume in one launch set
+            const OrderTables& tb = p->tabs.at(n);
             const int dft = has_fast_fft(n) ? 2 : 3;
+            const bool tiled = skew_tiled(tb);
+            const bool split_b = which == 0 && tiled && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
+            const int kinds = !tiled ? 1 : split_b ? 1 : (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
+            if (split_b) total += mix;
             const int64_t cv = which == 0 ? chunk_vols(p, n) : std::max<int64_t>(1, p->scratch_points / n3);
             for (int64_t v0 = 0; v0 < nv; v0 += cv)
-                total += (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
+                total += kinds * (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
         } else if (!is_double(p->dtype) && n > 1) {
             const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
             const int dft = has_fast_fft(n) ? 2 : 3;

@@ -34,7 +34,9 @@ struct TiledMixArgs {
     const float* mats;          // [ncls][24][24][2] core of this mode for every class
     const int8_t* wrap;         // [ncls][24][3]
     const uint32_t* canon_mask; // [ncls]
-    const float2* phase;        // [8n]
+    const float2* phase;        // [M]: exp(2 pi i e / M)
+    const int* uv;              // [24][3] W_g^T v of the plan's shift c = v / d (device)
+    int M;                      // d n
     // flat index of slot g of a free orbit: k . lin[g] + lin[g][3]; lin[g][0..2]
     // are the columns of W_g weighted by (n^2, n, 1), lin[g][3] the wrap offset
     int lin[24][4];
@@ -85,16 +87,38 @@ __device__ __forceinline__ int slot_exp(uint32_t rp, int M8) {
     return q < 0 ? q + M8 : q;
 }
 
+// The free-orbit core of one mode and the row-phase weights of a skew plan,
+// passed to its kernels as a __grid_constant__ parameter: with compile-time
+// slot indices they are read from the constant bank, as c_core and the
+// compile-time weights are for the shift (1/8, 0, 3/8).
+struct SkewCore {
+    float2 m[24][24];
+    int u[24][3];
+};
+
+// row-phase exponent of slot g for any shift: (W_g kO).v mod M from the
+// plan's weights (skew plans; the canonical kernels use slot_exp)
+__device__ __forceinline__ int skew_exp(const TiledMixArgs& a, uint32_t rp, int g) {
+    const int* u = a.uv + 3 * g;
+    const int q = rep_dot(rp, __ldg(u), __ldg(u + 1), __ldg(u + 2)) % a.M;
+    return q < 0 ? q + a.M : q;
+}
+
 // grid.x covers the tiles (kMixWarps per block), grid.y the volumes (pairs
 // of real volumes when PAIR: forward reads x1 + i x2 from volumes 2p, 2p+1
 // and writes Z to volume 2p of the complex output; inverse / adjoint read a
 // compact complex volume p and write Re / Im to real volumes 2p, 2p+1).
 // One warp's tile `tile` of volume `vol` (warp = threadIdx.x / 32 < kMixWarps
 // selects its shared-memory slot); a warp past ntiles returns at once.
-template <int MODE, bool RIN, bool ROUT, bool PAIR = false>
+// SKEW: a shifted transform DCT_n(r,s,t); free orbits take the core and
+// the row-phase weights of `sc`, boundary tiles their staged class core and
+// the plan's weights (the constant-memory free core and the compile-time
+// weights belong to the shift (1/8, 0, 3/8)).
+template <int MODE, bool RIN, bool ROUT, bool PAIR = false, bool SKEW = false>
 __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, float* __restrict__ out,
                                                const TiledMixArgs& a, int ntiles, int tile, int64_t vol,
-                                               int core_in_smem, const int64_t* voff, unsigned char* smem_raw) {
+                                               int core_in_smem, const int64_t* voff, unsigned char* smem_raw,
+                                               const SkewCore* sc = nullptr) {
     constexpr bool CIN = (MODE != MODE_FWD) || !RIN || PAIR;    // complex values in the core
     constexpr bool COUT = (MODE == MODE_FWD) || !ROUT || PAIR;  // complex values out of the core
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -180,7 +204,14 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
         if (MODE != MODE_FWD) {
             static_for<0, 24>([&](auto Gc) {
                 constexpr int g = decltype(Gc)::value;
-                const float2 R = __ldg(ph + slot_exp<g>(myrep, M8));
+                int q;
+                if constexpr (SKEW) {
+                    q = rep_dot(myrep, sc->u[g][0], sc->u[g][1], sc->u[g][2]) % a.M;
+                    q = q < 0 ? q + a.M : q;
+                } else {
+                    q = slot_exp<g>(myrep, M8);
+                }
+                const float2 R = __ldg(ph + q);
                 const float zr = xr[g], zi = xi[g];
                 xr[g] = R.x * zr + R.y * zi;  // conj(R) Z
                 xi[g] = R.x * zi - R.y * zr;
@@ -192,7 +223,9 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
                 float ar = 0.f, ai = 0.f;
 #pragma unroll
                 for (int h = 0; h < 24; ++h) {
-                    const float2 m = c_core[MODE][g][h];
+                    float2 m;
+                    if constexpr (SKEW) m = sc->m[g][h];
+                    else m = c_core[MODE][g][h];
                     ar = fmaf(m.x, xr[h], ar);
                     ai = fmaf(m.y, xr[h], ai);
                     if (CIN) {
@@ -201,7 +234,14 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
                     }
                 }
                 if (MODE == MODE_FWD) {
-                    const float2 R = __ldg(ph + slot_exp<g>(myrep, M8));
+                    int q;
+                    if constexpr (SKEW) {
+                        q = rep_dot(myrep, sc->u[g][0], sc->u[g][1], sc->u[g][2]) % a.M;
+                        q = q < 0 ? q + a.M : q;
+                    } else {
+                        q = slot_exp<g>(myrep, M8);
+                    }
+                    const float2 R = __ldg(ph + q);
                     *reinterpret_cast<float2*>(row + 2 * g) =
                         make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
                 } else if (ROUT && !PAIR) {
@@ -229,9 +269,14 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
                     }
                 }
                 if (MODE == MODE_FWD) {
-                    int q = (int)(myrep & 1023) * c_u[g][0] + (int)((myrep >> 10) & 1023) * c_u[g][1] +
+                    int q;
+                    if constexpr (SKEW) {
+                        q = skew_exp(a, myrep, g);
+                    } else {
+                        q = (int)(myrep & 1023) * c_u[g][0] + (int)((myrep >> 10) & 1023) * c_u[g][1] +
                             (int)((myrep >> 20) & 1023) * c_u[g][2];
-                    q = q < 0 ? q + M8 : q;
+                        q = q < 0 ? q + M8 : q;
+                    }
                     const float2 R = __ldg(ph + q);
                     *reinterpret_cast<float2*>(row + 2 * g) =
                         make_float2(a.scale * (R.x * ar - R.y * ai), a.scale * (R.x * ai + R.y * ar));
@@ -282,5 +327,13 @@ __global__ void __launch_bounds__(kMixThreads, 3) mix_tiled_kernel(const float* 
 inline size_t mix_tiled_smem(int) { return (size_t)kMixWarps * 32 * kMixRow * 4; }
 // launches over boundary tiles also stage one class core per warp
 inline size_t mix_tiled_smem_core(int n) { return mix_tiled_smem(n) + (size_t)kMixWarps * 1152 * 4; }
+
+// Skew plans (mix_skew.cu): tiles [tile0, ntiles) of `nvol` volumes (the
+// free tiles on sc, the boundary tiles on their staged class cores: a launch
+// covers one kind), `mode` with real input (forward) or real output (inverse
+// / adjoint) as given; volume v of in / out at v n^3 values of the real or
+// complex type.
+cudaError_t launch_mix_tiled_skew(const TiledMixArgs& a, const SkewCore& sc, int mode, bool real_io, const float* in,
+                                  float* out, int tile0, int ntiles, bool boundary, int64_t nvol, cudaStream_t st);
 
 }  // namespace fcc

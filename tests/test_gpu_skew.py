@@ -174,7 +174,7 @@ def test_skew_launch_count_matches_recorded_launches(case):
         rec = p.profile_read()
         p.profile(False)
         assert sum(c for _, c in rec.values()) == p.launches(which), rec
-        assert "orbit_mix_" + ("fwd", "inv", "adj")[which] in rec
+        assert "mix_skew_" + ("fwd", "inv", "adj")[which] in rec
 
 
 def test_skew_full_size_sampled_rows():
