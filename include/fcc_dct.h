@@ -140,6 +140,38 @@ fcc_status fcc_dct_adjoint(fcc_plan* plan, const void* in, void* out, void* stre
 fcc_status fcc_dct_forward_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
 fcc_status fcc_dct_inverse_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
 
+/*
+ * Hermitian-packed forward and inverse of real plans (FCC_R64, FCC_R32 and
+ * the tensor-core dtypes) at the canonical shift (1/8, 0, 3/8).
+ *
+ * For real x the rows of the explicit matrix of Def. 2 come in conjugate
+ * pairs: y[pi(i,l,q)] = conj(y[i,l,q]) with the involution
+ * pi(i,l,q) = ((i - l) mod n, (-l) mod n, (q - l) mod n), whose fixed points
+ * (row l = 0) carry real values.  So the n^3 complex values y = D x of a real
+ * volume are fixed by n^3 reals.  The packed volume (n^3 reals of the
+ * dtype's real type, point order (i,l,q)) holds at point a = (i,l,q)
+ *     Re y[a]    if 2l < n, or 2l = n and 2q < n   ("primary" points),
+ *     -Im y[a]   otherwise (= Im y at the primary partner pi(a)).
+ * Unpacking: y[a] = pk[a] + i pk[pi(a)] at a primary point (pk[a] when
+ * l = 0), y[a] = pk[pi(a)] - i pk[a] elsewhere.
+ *
+ * fcc_dct_forward_packed: in = coefficients (real), out = packed D x.
+ * fcc_dct_inverse_packed: in = a packed volume (it stands for a y with the
+ * conjugate symmetry above), out = D^{-1} y (real coefficients; exact
+ * inverse of the packed forward).  Both move half the bytes of the complex
+ * form's point values.  Buffers: points * sizeof(real) bytes each, device
+ * pointers, 16-byte aligned, not overlapping.  Errors: FCC_ERR_UNSUPPORTED
+ * for complex dtypes, skew plans and (inverse) singular plans;
+ * FCC_ERR_INVALID_ARG as for fcc_dct_forward; FCC_ERR_ALLOC when the first
+ * call cannot allocate its workspace (two chunks of complex intermediate per
+ * internal stream, held by the plan).  The *_host forms take host buffers as
+ * fcc_dct_forward_host does.
+ */
+fcc_status fcc_dct_forward_packed(fcc_plan* plan, const void* in, void* out, void* stream);
+fcc_status fcc_dct_inverse_packed(fcc_plan* plan, const void* in, void* out, void* stream);
+fcc_status fcc_dct_forward_packed_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
+fcc_status fcc_dct_inverse_packed_host(fcc_plan* plan, const void* host_in, void* host_out, void* stream);
+
 /* Number of volumes, total points (sum of n^3) and element counts of the
  * forward input / output, for sizing buffers. */
 int fcc_dct_batch(const fcc_plan* plan);
@@ -149,7 +181,7 @@ int64_t fcc_dct_in_bytes(const fcc_plan* plan);
 int64_t fcc_dct_out_bytes(const fcc_plan* plan);
 
 /* Kernel launches one forward / inverse call enqueues (for reporting). */
-int fcc_dct_launches(const fcc_plan* plan, int which /* 0 fwd, 1 inv, 2 adj */);
+int fcc_dct_launches(const fcc_plan* plan, int which /* 0 fwd, 1 inv, 2 adj, 3 fwd packed, 4 inv packed */);
 
 /*
  * Optional per-kernel timing.  When enabled, every kernel launch the plan

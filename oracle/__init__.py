@@ -21,6 +21,12 @@ Contents (each function names the passage it follows):
                          sums (over k and over w) exchanged and the inner
                          exponential sum over the grid done by a library FFT.
                          Pinned against ``dct_matrix`` in the tests.
+* ``conjugate_partner`` / ``pack_hermitian`` / ``unpack_hermitian`` -- the
+                         involution pi of the point grid under which the
+                         values of a real input come in conjugate pairs
+                         (-theta is a W-image of theta_pi(a) modulo Z^3,
+                         Lemma 1 / Def. 2 with Prop. 1 (iii)), and the layout
+                         that stores those n^3 complex values as n^3 reals.
 * ``chebyshev_recurrence`` -- an independent second evaluator: T_k from the
                          values x = T_100, y = T_010, z = T_001 through the
                          mother recurrence (Prop. 1 (iv)) with l = e_j and
@@ -287,3 +293,49 @@ def chebyshev_recurrence(kmax, x, y, z):
         return memo[k]
 
     return {(a, b, c): T((a, b, c)) for a in range(kmax) for b in range(kmax) for c in range(kmax)}
+
+
+# ---------------------------------------------------------------------------
+# Conjugate pairs of point values of a real input, and the packed layout.
+# ---------------------------------------------------------------------------
+
+def conjugate_partner(n):
+    """pi(i, l, q) = ((i - l) mod n, (-l) mod n, (q - l) mod n) as flat point
+    indices.  With c = (1/8, 0, 3/8): -theta_{i,l,q} differs from
+    theta_{pi(i,l,q)} by a W-image modulo Z^3, so for real x
+    (D x)[pi(a)] = conj((D x)[a]) (T_k is W-invariant, Prop. 1 (iii))."""
+    out = np.empty(n ** 3, dtype=np.int64)
+    for i in range(n):
+        for l in range(n):
+            for q in range(n):
+                out[(i * n + l) * n + q] = (((i - l) % n) * n + (-l) % n) * n + (q - l) % n
+    return out
+
+
+def packed_primary(n):
+    """Points whose real part the packed layout stores: 2l < n, or 2l = n and
+    2q < n (row l = 0, the fixed points of pi, included)."""
+    i, l, q = np.indices((n, n, n)).reshape(3, -1)   # flat point index (i n + l) n + q
+    return (2 * l < n) | ((2 * l == n) & (2 * q < n))
+
+
+def pack_hermitian(y, n):
+    """n^3 complex point values with y[pi(a)] = conj(y[a]) -> n^3 reals:
+    Re y[a] at primary points, -Im y[a] (the imaginary part at the primary
+    partner) elsewhere.  Works on the last axis of a batch [..., n^3]."""
+    y = np.asarray(y).reshape(-1, n ** 3)
+    prim = packed_primary(n)
+    return np.where(prim[None, :], y.real, -y.imag)
+
+
+def unpack_hermitian(pk, n):
+    """Inverse of pack_hermitian: y[a] = pk[a] + i pk[pi(a)] at a primary point
+    off the row l = 0, pk[a] on that row, pk[pi(a)] - i pk[a] elsewhere."""
+    pk = np.asarray(pk, dtype=np.float64).reshape(-1, n ** 3)
+    pi = conjugate_partner(n)
+    prim = packed_primary(n)
+    row0 = np.indices((n, n, n)).reshape(3, -1)[1] == 0
+    y = np.empty(pk.shape, dtype=np.complex128)
+    y[:, prim] = pk[:, prim] + 1j * np.where(row0[prim][None, :], 0.0, pk[:, pi[prim]])
+    y[:, ~prim] = pk[:, pi[~prim]] - 1j * pk[:, ~prim]
+    return y

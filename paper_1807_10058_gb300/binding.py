@@ -22,7 +22,8 @@ EXPORTS = [
     "fcc_status_string", "fcc_dct_destroy", "fcc_dct_describe", "fcc_dct_weyl_group",
     "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
     "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune", "fcc_dct_test_wait_timeout",
-    "fcc_dct_plan_skew", "fcc_dct_describe_skew",
+    "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
+    "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -55,7 +56,8 @@ def lib():
                                             ctypes.POINTER(i32), ctypes.POINTER(i32)] + [vp] * 7
         L.fcc_dct_describe_skew.restype = i32
         for f in ("fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint", "fcc_dct_forward_host",
-                  "fcc_dct_inverse_host", "fcc_dct_inverse_static"):
+                  "fcc_dct_inverse_host", "fcc_dct_inverse_static", "fcc_dct_forward_packed",
+                  "fcc_dct_inverse_packed", "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host"):
             getattr(L, f).argtypes = [vp, vp, vp, vp]
             getattr(L, f).restype = i32
         L.fcc_dct_batch.argtypes = [vp]
@@ -270,6 +272,39 @@ class Plan:
         if g.dtype != ct or g.numel() != self.points:
             raise ValueError("adjoint input must be %s with %d elements" % (ct, self.points))
         return self._call(lib().fcc_dct_adjoint, "fcc_dct_adjoint", g, out, not self.real_input)
+
+    def forward_packed(self, x, out=None):
+        """Hermitian-packed forward of a real plan: n^3 reals per volume
+        (fcc_dct_forward_packed; layout in include/fcc_dct.h)."""
+        rt, _ = self._torch_types()
+        if not self.real_input or x.dtype != rt or x.numel() != self.points:
+            raise ValueError("packed forward input must be %s with %d elements (real plans)" % (rt, self.points))
+        return self._call(lib().fcc_dct_forward_packed, "fcc_dct_forward_packed", x, out, False)
+
+    def inverse_packed(self, pk, out=None):
+        """Inverse of forward_packed (fcc_dct_inverse_packed)."""
+        rt, _ = self._torch_types()
+        if not self.real_input or pk.dtype != rt or pk.numel() != self.points:
+            raise ValueError("packed inverse input must be %s with %d elements (real plans)" % (rt, self.points))
+        return self._call(lib().fcc_dct_inverse_packed, "fcc_dct_inverse_packed", pk, out, False)
+
+    def forward_packed_host(self, x_host, pk_host):
+        """forward_packed with host tensors (as forward_host)."""
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        _check(lib().fcc_dct_forward_packed_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
+                                                 ctypes.c_void_p(pk_host.data_ptr()), ctypes.c_void_p(st)),
+               "fcc_dct_forward_packed_host")
+        return pk_host
+
+    def inverse_packed_host(self, pk_host, x_host):
+        """inverse_packed with host tensors (as forward_host)."""
+        import torch
+        st = torch.cuda.current_stream().cuda_stream
+        _check(lib().fcc_dct_inverse_packed_host(self.handle, ctypes.c_void_p(pk_host.data_ptr()),
+                                                 ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(st)),
+               "fcc_dct_inverse_packed_host")
+        return x_host
 
     def inverse_host(self, y_host, x_host):
         """End-to-end inverse with host tensors (see forward_host)."""

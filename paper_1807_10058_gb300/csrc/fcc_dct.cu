@@ -108,6 +108,9 @@ struct fcc_plan {
     std::map<int, OrderTables> tabs;
     void* scratch = nullptr;         // complex workspace for inverse / adjoint
     int64_t scratch_points = 0;
+    void* packed_ws = nullptr;       // complex workspace of the packed forward / inverse (first call)
+    int64_t packed_slot = 0;         // its complex values per internal stream
+    int packed_streams = 0;
     void* host_in_dev = nullptr;     // device staging for the *_host entry points
     void* host_out_dev = nullptr;
     cudaStream_t copy_in = nullptr, copy_out = nullptr;   // *_host: copies overlapping the transform
@@ -1104,6 +1107,155 @@ fcc_status run_group(fcc_plan* p, int which, const OrderTables& t, const T* in, 
     return s;
 }
 
+// --- Hermitian-packed forward / inverse of real volumes ----------------------
+// (layout: pair.cuh)
+
+template <typename T>
+fcc_status launch_pack(bool pack, int n, const T* src, T* dst, int64_t nvol, cudaStream_t st) {
+    const int64_t total = nvol * (int64_t)n * n * n;
+    if (total <= 0) return FCC_OK;
+    const int64_t blocks = (total + 255) / 256;
+    if (blocks > 0x7fffffffLL) return FCC_ERR_UNSUPPORTED;
+    ProfScope ps(pack ? "pack_hermitian" : "unpack_hermitian", st);
+    if (pack) pack_hermitian_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(src, dst, n, total);
+    else unpack_hermitian_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(src, dst, n, total);
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
+}
+
+// Workspace of the packed calls, allocated by the first one: per internal
+// stream a slot of 2 * scratch_points complex values, i.e. a chunk of pairs at
+// the paired forward's stride of 2 n^3 complex values per pair.
+fcc_status ensure_packed_ws(fcc_plan* p) {
+    if (p->packed_ws) return FCC_OK;
+    const int64_t slot = 2 * p->scratch_points;
+    const int streams = std::max(1, p->scratch_streams);
+    fcc_status s = dev_alloc(p, &p->packed_ws, (size_t)slot * 2 * real_size(p->dtype) * streams);
+    if (s == FCC_OK) {
+        p->packed_slot = slot;
+        p->packed_streams = streams;
+    }
+    return s;
+}
+
+// (the sizes the first packed call allocates, before it has run)
+int64_t packed_slot_of(const fcc_plan* p) { return p->packed_ws ? p->packed_slot : 2 * p->scratch_points; }
+int packed_streams_of(const fcc_plan* p) { return p->packed_ws ? p->packed_streams : std::max(1, p->scratch_streams); }
+
+int64_t packed_pairs_per_chunk(const fcc_plan* p, int n) {
+    const int64_t n3 = (int64_t)n * n * n;
+    return std::max<int64_t>(1, std::min<int64_t>(chunk_vols(p, n), packed_slot_of(p) / (2 * n3)));
+}
+
+// Paired fast path (orders with register DFT passes), chunks of pairs
+// round-robin over the internal streams.  Forward: the mixing writes Y of each
+// pair into the stream's slot, the slab pass transforms it there and the
+// pencil pass, fused with the split, writes the packed volumes 2p, 2p + 1.
+// Inverse: the pencil pass reads the packed pairs (fused with the merge into
+// W = v1 + i v2) into the slot, then the slab pass and the inverse mixing.
+fcc_status run_pairs_packed(fcc_plan* p, int which, const OrderTables& t, const float* in, float* out,
+                            int64_t npairs, cudaStream_t st) {
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    const int ns = std::min(p->nstreams, packed_streams_of(p));
+    const int64_t cp = packed_pairs_per_chunk(p, t.n);
+    const float2* tw = (const float2*)t.tw;
+    const bool tc = is_tc(p->dtype);
+    const bool tc_all = tc && t.tc_core_image;
+    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    fcc_status s = FCC_OK;
+    int c = 0;
+    for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
+        const int64_t np = std::min(cp, npairs - p0);
+        cudaStream_t ss = p->streams[c % ns];
+        float* ws = (float*)p->packed_ws + (size_t)(c % ns) * p->packed_slot * 2;
+        const float* src = in + 2 * p0 * n3;
+        float* dst = out + 2 * p0 * n3;
+        if (which == 0) {
+            s = tc ? launch_mix_tc_pairs(p, t, src, ws, np, ss)
+                   : launch_mix_tiled(t, MODE_FWD, true, false, src, ws, np, 1.f, ss, true);
+            if (!s) s = fast_fft(t.n, true, +1, (const float2*)ws, (float2*)ws, np, tw, 2 * n3, ss);
+            if (!s) {
+                ProfScope ps("fft_pencil_pair_packed", ss);
+                if (launch_fast_pencil_pair(t.n, (const float2*)ws, (float2*)dst, np, tw, 2 * n3, ss, true) != cudaSuccess)
+                    s = FCC_ERR_CUDA;
+            }
+        } else {
+            {
+                ProfScope ps("fft_pencil_merge_packed", ss);
+                if (launch_fast_pencil_merge(t.n, (const float2*)src, (float2*)ws, np, tw, ss, true) != cudaSuccess)
+                    s = FCC_ERR_CUDA;
+            }
+            if (!s) s = fast_fft(t.n, true, -1, (const float2*)ws, (float2*)ws, np, tw, n3, ss);
+            const float scale = (float)(1.0 / (double)n3);
+            if (!s && tc_all) s = launch_mix_tc_inv_pairs(p, t, MODE_INV, ws, dst, np, scale, ss);
+            else if (!s) s = launch_mix_tiled(t, MODE_INV, false, true, ws, dst, np, scale, ss, true);
+        }
+    }
+    for (int i = 0; i < ns; ++i) {
+        if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    return s;
+}
+
+bool packed_fast(const fcc_plan* p, int n, int64_t nvol) {
+    return !is_double(p->dtype) && has_fast_fft(n) && p->pairing && nvol >= 2;
+}
+
+// One run of volumes of equal order: the paired fast path where it applies;
+// every other volume (an unpaired last one, orders without register DFT
+// passes, FP64) goes through the complex transform in the packed workspace
+// and the (un)packing kernel on the caller's stream.
+template <typename T>
+fcc_status run_group_packed(fcc_plan* p, int which, const OrderTables& t, const T* in, T* out, int64_t nvol,
+                            cudaStream_t st) {
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    fcc_status s = FCC_OK;
+    int64_t v0 = 0;
+    if (packed_fast(p, t.n, nvol)) {
+        s = run_pairs_packed(p, which, t, (const float*)in, (float*)out, nvol / 2, st);
+        v0 = 2 * (nvol / 2);
+    }
+    T* ws = (T*)p->packed_ws;
+    const int64_t cv = std::max<int64_t>(1, packed_slot_of(p) * packed_streams_of(p) / n3);
+    for (; v0 < nvol && !s; v0 += cv) {
+        const int64_t nv = std::min(cv, nvol - v0);
+        if (which == 0) {
+            s = run_group<T>(p, 0, t, in + v0 * n3, ws, nv, st);
+            if (!s) s = launch_pack<T>(true, t.n, ws, out + v0 * n3, nv, st);
+        } else {
+            s = launch_pack<T>(false, t.n, in + v0 * n3, ws, nv, st);
+            if (!s) s = run_group<T>(p, 1, t, ws, out + v0 * n3, nv, st);
+        }
+    }
+    return s;
+}
+
+template <typename T>
+fcc_status run_packed(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t st) {
+    const T* in = (const T*)vin;
+    T* out = (T*)vout;
+    fcc_status s = FCC_OK;
+    int v = 0;
+    while (v < p->batch && !s) {
+        int e = v + 1;
+        while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
+        const OrderTables& t = p->tabs.at(p->orders[v]);
+        s = run_group_packed<T>(p, which, t, in + p->offset[v], out + p->offset[v], e - v, st);
+        v = e;
+    }
+    return s;
+}
+
+// The packed layout exists for real dtypes at the canonical shift (the
+// involution pi is a property of (1/8, 0, 3/8)).
+fcc_status packed_ok(const fcc_plan* p, int which) {
+    if (!is_real_in(p->dtype) || p->skew) return FCC_ERR_UNSUPPORTED;
+    if (which == 1 && !p->invertible) return FCC_ERR_UNSUPPORTED;
+    return FCC_OK;
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int64_t in_bytes(const fcc_plan* p, int which) {
@@ -1164,18 +1316,44 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
     return s == FCC_OK ? FCC_OK : fail(s);
 }
 
+fcc_status dispatch_packed(fcc_plan* p, int which, const void* in, void* out, void* stream) {
+    if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    if (*(volatile int*)p->h_status != 0) {   // as in dispatch
+        *(volatile int*)p->h_status = 0;
+        return fail(FCC_ERR_TIMEOUT);
+    }
+    fcc_status s = packed_ok(p, which);
+    if (s) return fail(s);
+    if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
+    const int64_t bytes = p->points * (int64_t)real_size(p->dtype);
+    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + bytes, b0 = (uintptr_t)out, b1 = b0 + bytes;
+    if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+    if (cur != p->device) cudaSetDevice(p->device);
+    s = ensure_packed_ws(p);
+    if (s == FCC_OK) {
+        g_prof_plan = p;
+        s = is_double(p->dtype) ? run_packed<double>(p, which, in, out, (cudaStream_t)stream)
+                                : run_packed<float>(p, which, in, out, (cudaStream_t)stream);
+        g_prof_plan = nullptr;
+    }
+    if (cur != p->device) cudaSetDevice(cur);
+    return s == FCC_OK ? FCC_OK : fail(s);
+}
+
 // Uniform plans: chunks of ~32 MB of volumes go through three streams -- the
 // copy in (copy_in), the transform (the caller's stream, forking as usual)
 // and the copy out (copy_out) -- so chunk c + 1 arrives and chunk c - 1
 // leaves while chunk c is transformed.  Each event is waited on right after
 // it is recorded, so one event per direction serves every chunk.
 template <typename T>
-fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hout, cudaStream_t st) {
+fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hout, cudaStream_t st, bool packed) {
     const int n = p->orders[0];
     const OrderTables& t = p->tabs.at(n);
     const int64_t n3 = (int64_t)n * n * n;
-    const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
-    const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
+    const int64_t rs_in = packed || (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
+    const int64_t rs_out = packed || (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t vin = n3 * rs_in * (int64_t)sizeof(T), vout = n3 * rs_out * (int64_t)sizeof(T);
     int64_t cv = std::max<int64_t>(2, (32ll << 20) / std::max(vin, vout));
     cv += cv % 2;   // whole pairs of real volumes
@@ -1192,7 +1370,8 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
             s = FCC_ERR_CUDA;
             break;
         }
-        s = run_group<T>(p, which, t, (const T*)(din + v0 * vin), (T*)(dout + v0 * vout), nv, st);
+        s = packed ? run_group_packed<T>(p, which, t, (const T*)(din + v0 * vin), (T*)(dout + v0 * vout), nv, st)
+                   : run_group<T>(p, which, t, (const T*)(din + v0 * vin), (T*)(dout + v0 * vout), nv, st);
         if (s) break;
         if (cudaEventRecord(p->ev_out, st) != cudaSuccess || cudaStreamWaitEvent(p->copy_out, p->ev_out, 0) != cudaSuccess ||
             cudaMemcpyAsync(hout + v0 * vout, dout + v0 * vout, nv * vout, cudaMemcpyDeviceToHost, p->copy_out) != cudaSuccess)
@@ -1204,11 +1383,13 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
     return s;
 }
 
-fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream) {
+fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream, bool packed = false) {
     if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
     if (which == 1 && !p->invertible) return fail(FCC_ERR_UNSUPPORTED);
+    if (packed && packed_ok(p, which)) return fail(packed_ok(p, which));
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t ib = in_bytes(p, which), ob = out_bytes(p, which);
+    const int64_t pk = p->points * (int64_t)real_size(p->dtype);   // a packed (or real) batch
+    const int64_t ib = packed ? pk : in_bytes(p, which), ob = packed ? pk : out_bytes(p, which);
     const int64_t cap = std::max(in_bytes(p, 0), in_bytes(p, 1));
     const int64_t capo = std::max(out_bytes(p, 0), out_bytes(p, 1));
     fcc_status s;
@@ -1218,17 +1399,97 @@ fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, vo
         int cur = 0;
         if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
         if (cur != p->device) cudaSetDevice(p->device);
+        s = packed ? ensure_packed_ws(p) : FCC_OK;
         g_prof_plan = p;
-        s = is_double(p->dtype) ? run_host_pipelined<double>(p, which, (const char*)hin, (char*)hout, st)
-                                : run_host_pipelined<float>(p, which, (const char*)hin, (char*)hout, st);
+        if (s == FCC_OK)
+            s = is_double(p->dtype) ? run_host_pipelined<double>(p, which, (const char*)hin, (char*)hout, st, packed)
+                                    : run_host_pipelined<float>(p, which, (const char*)hin, (char*)hout, st, packed);
         g_prof_plan = nullptr;
         if (cur != p->device) cudaSetDevice(cur);
         return s == FCC_OK ? FCC_OK : fail(s);
     }
     if (cudaMemcpyAsync(p->host_in_dev, hin, ib, cudaMemcpyHostToDevice, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
-    if ((s = dispatch(p, which, p->host_in_dev, p->host_out_dev, stream))) return s;
+    if ((s = packed ? dispatch_packed(p, which, p->host_in_dev, p->host_out_dev, stream)
+                    : dispatch(p, which, p->host_in_dev, p->host_out_dev, stream)))
+        return s;
     if (cudaMemcpyAsync(hout, p->host_out_dev, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(FCC_ERR_CUDA);
     return FCC_OK;
+}
+
+// Launches of one run of `nv` volumes of order n (run_group, excluding the
+// ragged fast paths).
+int group_launches(const fcc_plan* p, int which, int n, int64_t nv) {
+    int total = 0;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int mix = (int)((nv + 65534) / 65535);
+    if (!is_double(p->dtype) && n > 1 && p->skew) {
+        // run_group_skew: per chunk the mixing launches (free and boundary
+        // tiles, or the generic kernel) and the DFT passes; the forward
+        // mixes the boundary tiles of every volume in one launch set
+        const OrderTables& tb = p->tabs.at(n);
+        const int dft = has_fast_fft(n) ? 2 : 3;
+        const bool tiled = skew_tiled(tb);
+        const bool split_b = which == 0 && tiled && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
+        const int kinds = !tiled ? 1 : split_b ? 1 : (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
+        if (split_b) total += mix;
+        const int64_t cv = which == 0 ? chunk_vols(p, n) : std::max<int64_t>(1, p->scratch_points / n3);
+        for (int64_t v0 = 0; v0 < nv; v0 += cv)
+            total += kinds * (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
+    } else if (!is_double(p->dtype) && n > 1) {
+        const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
+        const int dft = has_fast_fft(n) ? 2 : 3;
+        const OrderTables& tb = p->tabs.at(n);
+        const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
+        const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
+        const bool tc_all = is_tc(p->dtype) && tb.tc_core_image;   // one launch mixes every tile
+        const int64_t npairs = pairing ? nv / 2 : 0;
+        // per paired chunk: mixing, then the DFT passes and the pair split /
+        // merge (the fast forward fuses the split into its pencil pass;
+        // generic passes over strided pairs go pair by pair)
+        const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles && !tc_all;
+        if (split_b) total += 1;
+        for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
+            const int64_t np = std::min(cv, npairs - p0);
+            // (the inverse / adjoint merge into a compact workspace first)
+            const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
+            total += (int)((split_b || tc_all ? 1 : mixl) + dft_pair);
+        }
+        const int64_t rest = nv - 2 * npairs;
+        total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
+    } else if (which == 0) total += mix + 3;
+    else {
+        const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
+        total += (int)((nv + chunk - 1) / chunk) * 4;
+    }
+    return total;
+}
+
+// Launches of the packed forward (which 0) / inverse (1): run_group_packed.
+int packed_launches(const fcc_plan* p, int which) {
+    if (packed_ok(p, which)) return 0;
+    int total = 0;
+    int v = 0;
+    while (v < p->batch) {
+        int e = v + 1;
+        while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
+        const int n = p->orders[v];
+        const int64_t n3 = (int64_t)n * n * n;
+        const int64_t nv = e - v;
+        int64_t v0 = 0;
+        if (packed_fast(p, n, nv)) {
+            const OrderTables& tb = p->tabs.at(n);
+            const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
+            const bool tc = is_tc(p->dtype), tc_all = tc && tb.tc_core_image;
+            const int per_chunk = (which == 0 ? (tc ? 1 : mixl) : (tc_all ? 1 : mixl)) + 2;
+            const int64_t npairs = nv / 2, cp = packed_pairs_per_chunk(p, n);
+            total += (int)((npairs + cp - 1) / cp) * per_chunk;
+            v0 = 2 * npairs;
+        }
+        const int64_t cv = std::max<int64_t>(1, packed_slot_of(p) * packed_streams_of(p) / n3);
+        for (; v0 < nv; v0 += cv) total += 1 + group_launches(p, which, n, std::min(cv, nv - v0));
+        v = e;
+    }
+    return total;
 }
 
 }  // namespace
@@ -1383,6 +1644,14 @@ fcc_status fcc_dct_inverse(fcc_plan* p, const void* in, void* out, void* stream)
 fcc_status fcc_dct_adjoint(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 2, in, out, stream); }
 fcc_status fcc_dct_forward_host(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_host(p, 0, in, out, stream); }
 fcc_status fcc_dct_inverse_host(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_host(p, 1, in, out, stream); }
+fcc_status fcc_dct_forward_packed(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_packed(p, 0, in, out, stream); }
+fcc_status fcc_dct_inverse_packed(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch_packed(p, 1, in, out, stream); }
+fcc_status fcc_dct_forward_packed_host(fcc_plan* p, const void* in, void* out, void* stream) {
+    return dispatch_host(p, 0, in, out, stream, true);
+}
+fcc_status fcc_dct_inverse_packed_host(fcc_plan* p, const void* in, void* out, void* stream) {
+    return dispatch_host(p, 1, in, out, stream, true);
+}
 
 int fcc_dct_batch(const fcc_plan* p) { return p ? p->batch : 0; }
 int64_t fcc_dct_points(const fcc_plan* p) { return p ? p->points : 0; }
@@ -1391,6 +1660,7 @@ int64_t fcc_dct_out_bytes(const fcc_plan* p) { return p ? out_bytes(p, 0) : 0; }
 
 int fcc_dct_launches(const fcc_plan* p, int which) {
     if (!p) return 0;
+    if (which == 3 || which == 4) return packed_launches(p, which - 3);
     int total = 0;
     if (!is_double(p->dtype) && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_ok(p, which)) {
         if (p->ragged_mode == 1 && ragged_persistent_ok(p)) return 1;
@@ -1404,49 +1674,7 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
     while (v < p->batch) {
         int e = v + 1;
         while (e < p->batch && p->orders[e] == p->orders[v]) ++e;
-        const int n = p->orders[v];
-        const int64_t n3 = (int64_t)n * n * n;
-        const int64_t nv = e - v;
-        const int mix = (int)((nv + 65534) / 65535);
-        if (!is_double(p->dtype) && n > 1 && p->skew) {
-            // run_group_skew: per chunk the mixing launches (free and boundary
-            // tiles, or the generic kernel) and the DFT passes; the forward
-            // mixes the boundary tiles of every volume in one launch set
-            const OrderTables& tb = p->tabs.at(n);
-            const int dft = has_fast_fft(n) ? 2 : 3;
-            const bool tiled = skew_tiled(tb);
-            const bool split_b = which == 0 && tiled && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
-            const int kinds = !tiled ? 1 : split_b ? 1 : (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
-            if (split_b) total += mix;
-            const int64_t cv = which == 0 ? chunk_vols(p, n) : std::max<int64_t>(1, p->scratch_points / n3);
-            for (int64_t v0 = 0; v0 < nv; v0 += cv)
-                total += kinds * (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
-        } else if (!is_double(p->dtype) && n > 1) {
-            const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
-            const int dft = has_fast_fft(n) ? 2 : 3;
-            const OrderTables& tb = p->tabs.at(n);
-            const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
-            const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
-            const bool tc_all = is_tc(p->dtype) && tb.tc_core_image;   // one launch mixes every tile
-            const int64_t npairs = pairing ? nv / 2 : 0;
-            // per paired chunk: mixing, then the DFT passes and the pair split /
-            // merge (the fast forward fuses the split into its pencil pass;
-            // generic passes over strided pairs go pair by pair)
-            const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles && !tc_all;
-            if (split_b) total += 1;
-            for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
-                const int64_t np = std::min(cv, npairs - p0);
-                // (the inverse / adjoint merge into a compact workspace first)
-                const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
-                total += (int)((split_b || tc_all ? 1 : mixl) + dft_pair);
-            }
-            const int64_t rest = nv - 2 * npairs;
-            total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
-        } else if (which == 0) total += mix + 3;
-        else {
-            const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
-            total += (int)((nv + chunk - 1) / chunk) * 4;
-        }
+        total += group_launches(p, which, p->orders[v], e - v);
         v = e;
     }
     return total;

@@ -37,41 +37,52 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
 
 template <int N>
 cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const float2* tw, int64_t vstride,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool packed) {
     using L = FastLayout<N>;
     if (vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
+    // packed: 4-byte stores to a separate output (the complex input is not overwritten in place)
+    if (packed && (((uintptr_t)out & 3u) != 0 || (const void*)in == (const void*)out)) return cudaErrorInvalidValue;
     static DeviceOnce attr;
     if (!attr.done()) {
         cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::pencil_smem);
         attr.mark();
     }
     const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
-    fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
+    if (packed) fft_pencil_pair_kernel<N, true><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
+    else fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
     return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const float2* tw, cudaStream_t st) {
+cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const float2* tw, cudaStream_t st,
+                           bool packed) {
     using L = FastLayout<N>;
+    if (packed && ((uintptr_t)in & 3u) != 0) return cudaErrorInvalidValue;
     static DeviceOnce attr;
     if (!attr.done()) {
         cudaFuncSetAttribute(fft_pencil_merge_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
+        cudaFuncSetAttribute(fft_pencil_merge_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L::pencil_smem);
         attr.mark();
     }
     const int64_t n3 = (int64_t)N * N * N;
     const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
-    fft_pencil_merge_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
+    // in_vstride 2 n^3: complex values per pair of complex volumes, or floats per pair of packed ones
+    if (packed) fft_pencil_merge_kernel<N, true><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
+    else fft_pencil_merge_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                     cudaStream_t st) {
+                                     cudaStream_t st, bool packed) {
     switch (n) {
-#define FCC_CASE(NN) case NN: return launch_merge_n<NN>(in, out, npairs, tw, st);
+#define FCC_CASE(NN) case NN: return launch_merge_n<NN>(in, out, npairs, tw, st, packed);
         FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
         FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
 #undef FCC_CASE
@@ -81,9 +92,9 @@ cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64
 }
 
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                    int64_t vstride, cudaStream_t st) {
+                                    int64_t vstride, cudaStream_t st, bool packed) {
     switch (n) {
-#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st);
+#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st, packed);
         FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
         FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
 #undef FCC_CASE

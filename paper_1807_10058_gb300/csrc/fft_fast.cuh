@@ -432,6 +432,12 @@ fft_pencil_kernel(const float2* in, float2* out, const float2* __restrict__ twg,
 // columns q < n/2 are primary, so every pencil is written exactly once.
 // grid.x = pairs * (n/2 + 1) * ceil(n / CPB2); Y of pair p sits at
 // p * vstride (vstride >= 2 n^3), y2 at p * vstride + n^3.
+//
+// PACKED: out holds real volumes (pair p at p * 2 n^3 floats, volume 2p + 1
+// n^3 floats after volume 2p) in the Hermitian-packed layout: a point of a
+// primary pencil stores Re y, a point of a partner pencil stores -Im y (the
+// imaginary part at its primary partner), so each of the n^3 reals of a
+// volume is written by the thread that owns its point.
 template <int N>
 struct PairLayout {
     static constexpr int PPW = FastLayout<N>::PPW;
@@ -439,7 +445,7 @@ struct PairLayout {
     static constexpr int CBLK = (N + CPB2 - 1) / CPB2;
 };
 
-template <int N>
+template <int N, bool PACKED = false>
 __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
     using L = FastLayout<N>;
@@ -468,6 +474,7 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     const int lo = partner ? (N - l) % N : l;
     const int co = partner ? (c - l + N) % N : c;
     const int64_t base = pr * vstride + (int64_t)lo * N + co;     // own pencil; + k * NN
+    const int64_t pbase = pr * 2 * N3 + (int64_t)lo * N + co;      // PACKED: own pencil of volume 2p
     float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     float ur[E][G], ui[E][G];
     if (!idle) {
@@ -512,7 +519,11 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
             const float2 B = cx[kc];
             const float Ar = ur[e][k1], Ai = ui[e][k1];
             const float dr = 0.5f * (Ar - B.x), di = 0.5f * (Ai + B.y);   // y2 = -i d
-            if (act) {
+            if (act && PACKED) {   // primary: Re y1, Re y2; partner: -Im y1, -Im y2
+                float* o = reinterpret_cast<float*>(out);
+                o[pbase + k * NN] = partner ? 0.5f * (B.y - Ai) : 0.5f * (Ar + B.x);
+                o[pbase + N3 + k * NN] = partner ? dr : di;
+            } else if (act) {
                 out[base + k * NN] = make_float2(0.5f * (Ar + B.x), 0.5f * (Ai - B.y));
                 out[base + N3 + k * NN] = make_float2(di, -dr);
             }
@@ -528,7 +539,14 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
 // every thread forms W at its own pencil and transforms it along the slow
 // axis with the - sign, written to the compact volume p at p * out_vstride.
 // Row 0's partner warps idle; in row n/2 only columns q < n/2 are primary.
-template <int N>
+//
+// PACKED: in holds Hermitian-packed real volumes (pair p at p * in_vstride
+// floats, volume 2p + 1 n^3 floats later; the layout of the packed forward).
+// A packed volume stands for a v with v o pi = conj v, so P(v) = v: at a
+// primary point v = (own, counterpart) (row 0: (own, 0)), at a partner point
+// v = (counterpart, -own); the two volumes' raw values meet in shared memory
+// together.
+template <int N, bool PACKED = false>
 __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ twg,
                         int64_t in_vstride, int64_t out_vstride) {
@@ -560,25 +578,19 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
     float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXPC;
     const int sh = partner ? l : N - l;   // counterpart index k + sh (mod N)
-    float v1r[R1], v1i[R1], v2r[R1], v2i[R1];
-#pragma unroll
-    for (int m = 0; m < R1; ++m) {
-        const int64_t o = (int64_t)(j + G * m) * NN;
-        const float2 a = act ? in[pin + o] : make_float2(0.f, 0.f);
-        const float2 b = act ? in[pin + N3 + o] : make_float2(0.f, 0.f);
-        v1r[m] = a.x;
-        v1i[m] = a.y;
-        v2r[m] = b.x;
-        v2i[m] = b.y;
-    }
     float wr[R1], wi[R1];
+    if (PACKED) {
+        const float* inf = reinterpret_cast<const float*>(in);
+        float p1[R1], p2[R1];
 #pragma unroll
-    for (int vv = 0; vv < 2; ++vv) {
-        const float* vr = vv ? v2r : v1r;
-        const float* vi = vv ? v2i : v1i;
+        for (int m = 0; m < R1; ++m) {
+            const int64_t o = (int64_t)(j + G * m) * NN;
+            p1[m] = act ? inf[pin + o] : 0.f;
+            p2[m] = act ? inf[pin + N3 + o] : 0.f;
+        }
         if (!idle) {
 #pragma unroll
-            for (int m = 0; m < R1; ++m) ex[j + G * m] = make_float2(vr[m], vi[m]);
+            for (int m = 0; m < R1; ++m) ex[j + G * m] = make_float2(p1[m], p2[m]);
         }
         __syncthreads();
         if (!idle) {
@@ -586,18 +598,54 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
             for (int m = 0; m < R1; ++m) {
                 int kc = j + G * m + sh;
                 kc -= kc >= N ? N : 0;
-                const float2 B = cx[kc];
-                const float pr_ = 0.5f * (vr[m] + B.x), pi_ = 0.5f * (vi[m] - B.y);   // P(v) at this point
-                if (vv == 0) {
-                    wr[m] = pr_;
-                    wi[m] = pi_;
-                } else {   // W = P(v1) + i P(v2)
-                    wr[m] -= pi_;
-                    wi[m] += pr_;
-                }
+                const float2 C = cx[kc];
+                const float c1 = l == 0 ? 0.f : C.x, c2 = l == 0 ? 0.f : C.y;
+                const float v1r = partner ? C.x : p1[m], v1i = partner ? -p1[m] : c1;
+                const float v2r = partner ? C.y : p2[m], v2i = partner ? -p2[m] : c2;
+                wr[m] = v1r - v2i;   // W = v1 + i v2
+                wi[m] = v1i + v2r;
             }
         }
-        __syncthreads();
+        __syncthreads();   // counterpart reads done before the exchange buffers are reused
+    } else {
+        float v1r[R1], v1i[R1], v2r[R1], v2i[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+            const int64_t o = (int64_t)(j + G * m) * NN;
+            const float2 a = act ? in[pin + o] : make_float2(0.f, 0.f);
+            const float2 b = act ? in[pin + N3 + o] : make_float2(0.f, 0.f);
+            v1r[m] = a.x;
+            v1i[m] = a.y;
+            v2r[m] = b.x;
+            v2i[m] = b.y;
+        }
+#pragma unroll
+        for (int vv = 0; vv < 2; ++vv) {
+            const float* vr = vv ? v2r : v1r;
+            const float* vi = vv ? v2i : v1i;
+            if (!idle) {
+#pragma unroll
+                for (int m = 0; m < R1; ++m) ex[j + G * m] = make_float2(vr[m], vi[m]);
+            }
+            __syncthreads();
+            if (!idle) {
+#pragma unroll
+                for (int m = 0; m < R1; ++m) {
+                    int kc = j + G * m + sh;
+                    kc -= kc >= N ? N : 0;
+                    const float2 B = cx[kc];
+                    const float pr_ = 0.5f * (vr[m] + B.x), pi_ = 0.5f * (vi[m] - B.y);   // P(v) at this point
+                    if (vv == 0) {
+                        wr[m] = pr_;
+                        wi[m] = pi_;
+                    } else {   // W = P(v1) + i P(v2)
+                        wr[m] -= pi_;
+                        wi[m] += pr_;
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
     if (idle) return;   // no block barrier below
     PencilFft<N, -1>::run(wr, wi, j, ex, tw, [&](int k, float xr, float xi) {
@@ -611,10 +659,12 @@ cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2
                             const float2* tw, int64_t vstride, const int64_t* voff, cudaStream_t st);
 // inverse / adjoint: pair merge + first (pencil) pass, pairs at p * 2 n^3 of in,
 // compact results at p * n^3 of out
+// (packed: in holds Hermitian-packed real volumes, pair p at p * 2 n^3 floats)
 cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                     cudaStream_t st);
+                                     cudaStream_t st, bool packed = false);
 // forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
+// (packed: out receives Hermitian-packed real volumes, pair p at p * 2 n^3 floats)
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                    int64_t vstride, cudaStream_t st);
+                                    int64_t vstride, cudaStream_t st, bool packed = false);
 
 }  // namespace fcc

@@ -66,4 +66,52 @@ __global__ void pair_merge_kernel(const float2* __restrict__ y, float2* __restri
     W[b] = make_float2(P1.x + P2.y, -P1.y + P2.x);
 }
 
+// --- Hermitian-packed layout of real-input transforms ----------------------
+//
+// For real x the n^3 complex values y = D x are determined by n^3 reals: on
+// each pair {a, pi(a)} y[pi(a)] = conj(y[a]), and at the fixed points of pi
+// (the row l = 0) y is real.  The packed volume stores, at every point
+// a = (i, l, q),
+//   Re y[a]   if a is primary: 2l < n, or 2l = n and 2q < n (this includes
+//             the fixed points, l = 0),
+//   -Im y[a]  otherwise (= Im y at its primary partner pi(a)).
+// Unpacking: at a primary a, y[a] = pk[a] + i pk[pi(a)] (l = 0: pk[a]); at
+// any other point y[a] = pk[pi(a)] - i pk[a].  The fast DFT passes use the
+// same split into primary and partner pencils (fft_pencil_pair_kernel,
+// fft_pencil_merge_kernel).
+__host__ __device__ __forceinline__ bool packed_primary(int l, int q, int n) {
+    return 2 * l < n || (2 * l == n && 2 * q < n);
+}
+
+// complex y (nvol volumes of n^3) -> packed reals pk
+template <typename T>
+__global__ void pack_hermitian_kernel(const T* __restrict__ y, T* __restrict__ pk, int n, int64_t total) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int q = (int)(t % n);
+    const int l = (int)((t / n) % n);
+    pk[t] = packed_primary(l, q, n) ? y[2 * t] : -y[2 * t + 1];
+}
+
+// packed reals pk -> complex y (nvol volumes of n^3)
+template <typename T>
+__global__ void unpack_hermitian_kernel(const T* __restrict__ pk, T* __restrict__ y, int n, int64_t total) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int64_t r = t % n3, vb = t - r;
+    const int q = (int)(r % n);
+    const int l = (int)((r / n) % n);
+    const int i = (int)(r / ((int64_t)n * n));
+    const int i2 = (i - l + n) % n, l2 = (n - l) % n, q2 = (q - l + n) % n;
+    const T own = pk[t], other = pk[vb + ((int64_t)i2 * n + l2) * n + q2];
+    if (packed_primary(l, q, n)) {
+        y[2 * t] = own;
+        y[2 * t + 1] = l == 0 ? T(0) : other;
+    } else {
+        y[2 * t] = other;
+        y[2 * t + 1] = -own;
+    }
+}
+
 }  // namespace fcc

@@ -67,7 +67,8 @@ def test_invalid_skew_plan_arguments(v, d, dtype, status):
 def test_null_plan_calls():
     L = binding.lib()
     for f in (L.fcc_dct_forward, L.fcc_dct_inverse, L.fcc_dct_adjoint, L.fcc_dct_forward_host,
-              L.fcc_dct_inverse_host):
+              L.fcc_dct_inverse_host, L.fcc_dct_forward_packed, L.fcc_dct_inverse_packed,
+              L.fcc_dct_forward_packed_host, L.fcc_dct_inverse_packed_host):
         assert f(None, None, None, None) == binding.FCC_ERR_INVALID_ARG
     assert L.fcc_dct_batch(None) == 0 and L.fcc_dct_points(None) == 0
     L.fcc_dct_destroy(None)

@@ -55,3 +55,24 @@ def test_dropped_normalisation_is_caught():
     th = RNG.random(3)
     t0 = oracle.chebyshev((0, 0, 0), th)
     assert abs(t0 - 1) < 1e-15 and abs(24 * t0 - 1) > 1
+
+
+def test_wrong_packed_rule_is_caught(monkeypatch):
+    """Row n/2 taken whole as primary (both points of its pairs) or the
+    partner map with the wrong sign of the slow shift: the packed round trip
+    of D x breaks."""
+    n = 4
+    D = oracle.dct_matrix(n)
+    x = RNG.standard_normal(n ** 3)
+    y = D @ x
+    good = oracle.unpack_hermitian(oracle.pack_hermitian(y, n), n)[0]
+    assert np.abs(good - y).max() < 1e-12
+    keep = oracle.packed_primary
+    monkeypatch.setattr(oracle, "packed_primary",
+                        lambda m: np.array([2 * ((a // m) % m) <= m for a in range(m ** 3)]))
+    assert np.abs(oracle.unpack_hermitian(oracle.pack_hermitian(y, n), n)[0] - y).max() > 1e-3
+    monkeypatch.setattr(oracle, "packed_primary", keep)
+    bad_pi = np.array([((((a // (n * n)) + (a // n) % n) % n) * n + (-(a // n)) % n) * n + (a % n - (a // n) % n) % n
+                       for a in range(n ** 3)])
+    monkeypatch.setattr(oracle, "conjugate_partner", lambda m: bad_pi)
+    assert np.abs(oracle.unpack_hermitian(oracle.pack_hermitian(y, n), n)[0] - y).max() > 1e-3

@@ -311,3 +311,30 @@ def test_pairing_identities(n):
     P = (y + np.conj(y[pi])) / 2
     assert np.abs(np.linalg.solve(D, P) - np.linalg.solve(D, y).real).max() < 1e-12
     assert np.abs(D.conj().T @ P - (D.conj().T @ y).real).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_packed_layout_keeps_exactly_the_point_values(n):
+    """The packed layout of real inputs: the oracle's pi pairs the rows of the
+    dense matrix of Def. 2 into conjugates, every 2-cycle of pi has exactly one
+    primary point and every fixed point (row l = 0, n^2 of them) is primary,
+    unpack(pack(D x)) = D x, D^-1 unpack(pack(D x)) = x, and every real
+    vector is the packing of exactly one conjugate-symmetric vector."""
+    D = oracle.dct_matrix(n)
+    pi = oracle.conjugate_partner(n)
+    prim = oracle.packed_primary(n)
+    assert np.abs(D[pi] - np.conj(D)).max() < 1e-13
+    fixed = pi == np.arange(n ** 3)
+    assert fixed.sum() == n * n
+    assert prim[fixed].all()
+    assert (prim[~fixed] != prim[pi[~fixed]]).all()
+    x = RNG.standard_normal((3, n ** 3))
+    y = (D @ x.T).T
+    pk = oracle.pack_hermitian(y, n)
+    assert pk.shape == (3, n ** 3) and pk.dtype == np.float64
+    assert np.abs(oracle.unpack_hermitian(pk, n) - y).max() < 1e-13 * max(1.0, np.abs(y).max())
+    assert np.abs(np.linalg.solve(D, oracle.unpack_hermitian(pk, n).T).T - x).max() < 1e-11
+    r = RNG.standard_normal(n ** 3)
+    u = oracle.unpack_hermitian(r, n)[0]
+    assert np.abs(u[pi] - np.conj(u)).max() == 0
+    assert np.abs(oracle.pack_hermitian(u, n)[0] - r).max() == 0
