@@ -27,6 +27,10 @@ Contents (each function names the passage it follows):
                          (-theta is a W-image of theta_pi(a) modulo Z^3,
                          Lemma 1 / Def. 2 with Prop. 1 (iii)), and the layout
                          that stores those n^3 complex values as n^3 reals.
+* ``oracle.radix2``   -- the radix-2x2x2 factorisation of Sec. 4.B (eq.
+                         FastAlgorithm) with the basis change B_n derived
+                         from its definition; a second, recursive FP64
+                         evaluation of the transform at n = 2^k.
 * ``chebyshev_recurrence`` -- an independent second evaluator: T_k from the
                          values x = T_100, y = T_010, z = T_001 through the
                          mother recurrence (Prop. 1 (iv)) with l = e_j and
