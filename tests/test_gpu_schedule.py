@@ -80,12 +80,12 @@ def test_persistent_ragged_launch_in_cuda_graph():
 def test_schedule_arguments_are_checked():
     with binding.Plan(32, 2, "r32") as p:
         L = binding.lib()
-        for key, bad in ((0, 0), (0, 2000), (1, 0), (1, 5), (2, 3), (3, 5), (9, 1)):
+        for key, bad in ((0, 0), (0, 2000), (1, 0), (1, 5), (2, 3), (3, 5), (4, 2), (4, -1), (9, 1)):
             assert L.fcc_dct_set_schedule(p.handle, key, bad) == binding.FCC_ERR_INVALID_ARG
         # one persistent launch is for ragged plans only
         assert L.fcc_dct_set_schedule(p.handle, 2, 1) == binding.FCC_ERR_UNSUPPORTED
         assert L.fcc_dct_get_schedule(p.handle, 9) == -1
-        assert p.schedule() == {"chunk_mb": 32, "streams": 2, "ragged": 0, "tc_blocks": 0}
+        assert p.schedule() == {"chunk_mb": 32, "streams": 2, "ragged": 0, "tc_blocks": 0, "tc_gather": 0}
 
 
 @pytest.mark.parametrize("dtype", ["r32", "r32_bf16x3"])
