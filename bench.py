@@ -486,7 +486,7 @@ def main():
     paired = args.dtype.startswith("r") and batch >= 2
     if paired:
         algo_bytes = {"mix_tiled_fwd": 8, "mix_tc_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12,
-                      "fft_pencil_pair": 12, "interleave_pairs": 8}
+                      "fft_pencil_pair": 12}
     else:
         algo_bytes = {"mix_tiled_fwd": 12, "fft_slab": 16, "fft_pencil": 16, "orbit_mix_fwd": 12,
                       "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16}

@@ -268,13 +268,6 @@ fcc_status fcc_dct_test_wait_timeout(fcc_plan* plan, int enable);
  *                                  run of equal orders
  *   FCC_SCHED_TC_BLOCKS  0..4      tensor-core mixing: blocks per SM in the
  *                                  grid (0 = as many as can be resident)
- *   FCC_SCHED_TC_GATHER  0, 1      tensor-core forward mixing of uniform
- *                                  plans: 0 = two 4-byte gathers per slot,
- *                                  one from each real volume of a pair; 1 =
- *                                  a copy pass first stages each pair as
- *                                  (x1, x2) 8-byte values in the unused half
- *                                  of its output region (or workspace slot),
- *                                  then one 8-byte gather per slot
  * set_schedule returns FCC_ERR_INVALID_ARG for an unknown key or a value out
  * of range; get_schedule returns the current value, or -1 on a bad argument.
  */
@@ -282,8 +275,7 @@ typedef enum {
     FCC_SCHED_CHUNK_MB = 0,
     FCC_SCHED_STREAMS = 1,
     FCC_SCHED_RAGGED = 2,
-    FCC_SCHED_TC_BLOCKS = 3,
-    FCC_SCHED_TC_GATHER = 4
+    FCC_SCHED_TC_BLOCKS = 3
 } fcc_sched_key;
 fcc_status fcc_dct_set_schedule(fcc_plan* plan, int key, int value);
 int fcc_dct_get_schedule(const fcc_plan* plan, int key);

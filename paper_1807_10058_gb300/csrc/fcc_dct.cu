@@ -124,7 +124,6 @@ struct fcc_plan {
     bool ragged_fast = true;         // ragged FP32 forward: per-order launches over offset tables
     int ragged_mode = 0;             // FCC_SCHED_RAGGED: 0 per-order launches, 1 one persistent launch, 2 per run of volumes
     int tc_blocks = 0;               // FCC_SCHED_TC_BLOCKS: tensor-core mixing blocks per SM in the grid (0 = resident maximum)
-    int tc_gather = 0;               // FCC_SCHED_TC_GATHER: 1 = stage each pair interleaved, one 8-byte gather per slot
     int wait_test = 0;               // fcc_dct_test_wait_timeout
     int scratch_streams = 1;         // internal streams the inverse / adjoint workspace was sized for
     int num_sms = 1;
@@ -759,37 +758,18 @@ fcc_status merge_dft3_pairs(const OrderTables& t, const float* y, float* ws, int
     return s ? s : launch_dft3(t, -1, ws, ws, np, st);
 }
 
-// The interleaved staging of FCC_SCHED_TC_GATHER applies (uniform plans:
-// chunk bases stay 16-byte aligned; n^3 a multiple of 4 for the quad copies).
-bool tc_interleave(const fcc_plan* p, int n) {
-    return p->tc_gather == 1 && p->uniform && ((int64_t)n * n * n) % 4 == 0;
-}
-
-// Launches of launch_mix_tc_pairs per 65535 pairs.
-int tc_mix_launches(const fcc_plan* p, const OrderTables& t) {
-    if (!t.tc_core_image) return 1;
-    return t.free_tiles > 0 ? 1 + (tc_interleave(p, t.n) ? 1 : 0) : 0;
-}
-
 // Forward mixing of `np` pairs of real volumes with the orbit core on the
-// tensor cores (every tile class; the SIMT kernel when the order has no free
-// orbits).  With FCC_SCHED_TC_GATHER = 1 each pair is first staged
-// interleaved in the second half of its output region.
+// tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
                                cudaStream_t st) {
     TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
     const bool bf16 = is_bf16(p->dtype);
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
-    const bool il = tc_interleave(p, t.n) && ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
     set_mix_tiled_attributes();
     static DeviceOnce attr;
     if (!attr.done()) {
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<0>::smem);
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<1>::smem);
-        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TcLayout<0>::smem);
-        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TcLayout<1>::smem);
         attr.mark();
     }
     for (int64_t v0 = 0; v0 < np; v0 += 65535) {
@@ -803,25 +783,13 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, lim) : lim;
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
             dim3 grid((unsigned)gx, (unsigned)nv);
-            if (il) {
-                ProfScope ps("interleave_pairs", st);
-                interleave_pairs_kernel<<<dim3((unsigned)((a.n3 / 4 + 255) / 256), (unsigned)nv), 256, 0, st>>>(
-                    src, (float2*)dst + a.n3, a.n3);
-            }
             ProfScope ps("mix_tc_fwd", st);
-            const uint4* ci = (const uint4*)t.tc_core_image;
-            if (bf16 && il)
-                mix_tc_fwd_pair_kernel<0, true><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
-                                                                                p->d_status, bnd, p->wait_test);
-            else if (bf16)
-                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
-                                                                          p->d_status, bnd, p->wait_test);
-            else if (il)
-                mix_tc_fwd_pair_kernel<1, true><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
-                                                                                p->d_status, bnd, p->wait_test);
+            if (bf16)
+                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
             else
-                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
-                                                                          p->d_status, bnd, p->wait_test);
+                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
+                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
         }
         if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
@@ -1484,7 +1452,7 @@ int group_launches(const fcc_plan* p, int which, int n, int64_t nv) {
             const int64_t np = std::min(cv, npairs - p0);
             // (the inverse / adjoint merge into a compact workspace first)
             const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
-            total += (int)((split_b ? 1 : tc_all ? (which == 0 ? tc_mix_launches(p, tb) : 1) : mixl) + dft_pair);
+            total += (int)((split_b || tc_all ? 1 : mixl) + dft_pair);
         }
         const int64_t rest = nv - 2 * npairs;
         total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
@@ -1512,7 +1480,7 @@ int packed_launches(const fcc_plan* p, int which) {
             const OrderTables& tb = p->tabs.at(n);
             const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
             const bool tc = is_tc(p->dtype), tc_all = tc && tb.tc_core_image;
-            const int per_chunk = (which == 0 ? (tc ? tc_mix_launches(p, tb) : mixl) : (tc_all ? 1 : mixl)) + 2;
+            const int per_chunk = (which == 0 ? (tc ? 1 : mixl) : (tc_all ? 1 : mixl)) + 2;
             const int64_t npairs = nv / 2, cp = packed_pairs_per_chunk(p, n);
             total += (int)((npairs + cp - 1) / cp) * per_chunk;
             v0 = 2 * npairs;
@@ -1574,10 +1542,6 @@ fcc_status fcc_dct_set_schedule(fcc_plan* p, int key, int value) {
             if (value < 0 || value > 4) return fail(FCC_ERR_INVALID_ARG);
             p->tc_blocks = value;
             return FCC_OK;
-        case FCC_SCHED_TC_GATHER:
-            if (value < 0 || value > 1) return fail(FCC_ERR_INVALID_ARG);
-            p->tc_gather = value;
-            return FCC_OK;
         default:
             return fail(FCC_ERR_INVALID_ARG);
     }
@@ -1590,7 +1554,6 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
         case FCC_SCHED_STREAMS: return p->nstreams;
         case FCC_SCHED_RAGGED: return p->ragged_mode;
         case FCC_SCHED_TC_BLOCKS: return p->tc_blocks;
-        case FCC_SCHED_TC_GATHER: return p->tc_gather;
         default: return -1;
     }
 }
@@ -1598,17 +1561,17 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
 fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream, int reps, float* best_ms) {
     if (!p || !in || !out || reps < 1 || reps > 100) return fail(FCC_ERR_INVALID_ARG);
     cudaStream_t st = (cudaStream_t)stream;
-    struct Cand { int chunk_mb, streams, ragged, tc, gather; };
+    struct Cand { int chunk_mb, streams, ragged, tc; };
     std::vector<Cand> cands;
-    const int tc0 = p->tc_blocks, g0 = p->tc_gather;
+    const int tc0 = p->tc_blocks;
     if (!p->uniform) {
         const bool fast = !is_double(p->dtype) && ragged_fast_ok(p, 0);
-        for (int ns = 1; ns <= kMaxStreams && fast; ++ns) cands.push_back({32, ns, 0, tc0, g0});
-        if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0, g0});
-        cands.push_back({32, 2, 2, tc0, g0});
+        for (int ns = 1; ns <= kMaxStreams && fast; ++ns) cands.push_back({32, ns, 0, tc0});
+        if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0});
+        cands.push_back({32, 2, 2, tc0});
     } else {
         for (int mb : {8, 16, 32, 64})
-            for (int ns = 1; ns <= kMaxStreams; ++ns) cands.push_back({mb, ns, 0, tc0, g0});
+            for (int ns = 1; ns <= kMaxStreams; ++ns) cands.push_back({mb, ns, 0, tc0});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1616,13 +1579,12 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
         cudaGetLastError();
         return fail(FCC_ERR_CUDA);
     }
-    const Cand saved = {(int)(p->chunk_bytes >> 20), p->nstreams, p->ragged_mode, p->tc_blocks, p->tc_gather};
+    const Cand saved = {(int)(p->chunk_bytes >> 20), p->nstreams, p->ragged_mode, p->tc_blocks};
     auto apply = [&](const Cand& c) {
         p->chunk_bytes = (int64_t)c.chunk_mb << 20;
         p->nstreams = c.streams;
         p->ragged_mode = c.ragged;
         p->tc_blocks = c.tc;
-        p->tc_gather = c.gather;
     };
     auto time_it = [&](const Cand& c, float& ms) -> bool {
         apply(c);
@@ -1654,17 +1616,8 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
             best = c;
         }
     }
-    // tensor-core forms: then the gather form and the grid of the mixing kernel
+    // tensor-core forms: then the grid of the mixing kernel
     if (p->uniform && is_tc(p->dtype) && best_t >= 0.f) {
-        {
-            Cand c = best;
-            c.gather = 1 - c.gather;
-            float ms = 0.f;
-            if (time_it(c, ms) && ms < best_t) {
-                best_t = ms;
-                best = c;
-            }
-        }
         for (int tcb : {2, 3, 4}) {
             Cand c = best;
             c.tc = tcb;

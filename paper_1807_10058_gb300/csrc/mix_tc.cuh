@@ -130,41 +130,18 @@ __device__ __forceinline__ void store_half(unsigned char* X, int row, const floa
 
 // Loads of slots H .. H + 11 of representative rp (both volumes of the pair).
 // off: per-slot wrap offsets of a boundary class (nullptr: the free class's,
-// a.lin[g][3]).  IL: the pair is staged interleaved, (x1, x2) as one 8-byte
-// value per point at il (interleave_pairs_kernel), one load per slot.
-template <int H, bool BND, bool IL>
-__device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* in0, const float* in1,
-                                            const float2* il, uint32_t rp, const int* off, float* vr, float* vi) {
+// a.lin[g][3]).
+template <int H, bool BND>
+__device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* in0, const float* in1, uint32_t rp,
+                                            const int* off, float* vr, float* vi) {
     const bool act = rp != 0xffffffffu;
     static_for<0, 12>([&](auto Sc) {
         constexpr int g = H + decltype(Sc)::value;
         const int o = BND ? __ldg(off + g) : a.lin[g][3];
         const int gi = act ? rep_dot(rp, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + o : 0;
-        if (IL) {
-            const float2 v = act ? __ldg(il + gi) : make_float2(0.f, 0.f);
-            vr[g - H] = v.x;
-            vi[g - H] = v.y;
-        } else {
-            vr[g - H] = act ? __ldg(in0 + gi) : 0.f;
-            vi[g - H] = act ? __ldg(in1 + gi) : 0.f;
-        }
+        vr[g - H] = act ? __ldg(in0 + gi) : 0.f;
+        vi[g - H] = act ? __ldg(in1 + gi) : 0.f;
     });
-}
-
-// Stages each pair of real volumes interleaved for the IL gathers: pair p of
-// x (volumes 2p, 2p + 1 at p * 2 n^3 floats) -> (x1[k], x2[k]) at
-// il + p * 2 n^3 + k (float2), i.e. the second half of the pair's complex
-// output region, which the mixing does not write.  n^3 % 4 == 0; 16-byte
-// aligned x and il.
-__global__ void interleave_pairs_kernel(const float* __restrict__ x, float2* __restrict__ il, int64_t n3) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // quad of points
-    if (4 * q >= n3) return;
-    const int64_t p = blockIdx.y;
-    const float4 a = __ldg(reinterpret_cast<const float4*>(x + p * 2 * n3) + q);
-    const float4 b = __ldg(reinterpret_cast<const float4*>(x + p * 2 * n3 + n3) + q);
-    float4* o = reinterpret_cast<float4*>(il + p * 2 * n3 + 4 * q);
-    o[0] = make_float4(a.x, b.x, a.y, b.y);
-    o[1] = make_float4(a.z, b.z, a.w, b.w);
 }
 
 // Epilogue for slots H .. H + 11 of this thread's orbit: TMEM columns 4H ..
@@ -221,9 +198,7 @@ struct TcBoundary {
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 // wait_test: issue no MMA and no completion signal, so that the (shortened)
 // wait runs out -- the test of the timeout path; nothing is written then.
-// IL: gather from the interleaved staging of each pair at out (as float2) +
-// pair * 2 n^3 + n^3 instead of from `in`.
-template <int KIND, bool IL = false>
+template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
                        const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status,
@@ -264,7 +239,6 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     const uint32_t kNone = 0xffffffffu;
     const float* __restrict__ in0 = in + pb;
     const float* __restrict__ in1 = in + pb + a.n3;
-    const float2* il = reinterpret_cast<const float2*>(out) + pb + a.n3;
     const int nall = ngroups + bnd.ngroups;
     // class of group g (block-uniform; free class for the free groups)
     auto cls_of = [&](int g) -> int { return g < ngroups || g >= nall ? a.free_class : __ldg(bnd.group + 8 * (g - ngroups)); };
@@ -280,12 +254,12 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     float vr[12], vi[12];
     auto gather = [&](uint32_t rp, int c) {   // warp-uniform branches: slot half, free or boundary class
         if (c == a.free_class) {
-            if (half == 0) gather_half<0, false, IL>(a, in0, in1, il, rp, nullptr, vr, vi);
-            else gather_half<12, false, IL>(a, in0, in1, il, rp, nullptr, vr, vi);
+            if (half == 0) gather_half<0, false>(a, in0, in1, rp, nullptr, vr, vi);
+            else gather_half<12, false>(a, in0, in1, rp, nullptr, vr, vi);
         } else {
             const int* off = bnd.off + 24 * c;
-            if (half == 0) gather_half<0, true, IL>(a, in0, in1, il, rp, off, vr, vi);
-            else gather_half<12, true, IL>(a, in0, in1, il, rp, off, vr, vi);
+            if (half == 0) gather_half<0, true>(a, in0, in1, rp, off, vr, vi);
+            else gather_half<12, true>(a, in0, in1, rp, off, vr, vi);
         }
     };
 
