@@ -204,24 +204,36 @@ FORM_NAMES = {"r32": "plain FP32 (SIMT orbit cores)",
 
 
 def sampled_accuracy(x, y, n, dev, rows=24, skew=None):
-    """Relative L2 error against the FP64 oracle, estimated from uniformly
-    sampled whole rows of D on the first volume (an unbiased estimate of the
-    whole-output relative L2), and the largest sampled error."""
+    """An accuracy probe of a GPU result: the first input volume, uniformly
+    sampled output rows and the GPU's values there, and the RMS of the first
+    output volume.  The oracle evaluates probes in the CPU leg
+    (evaluate_probes); uniform rows give an unbiased estimate of the
+    whole-output relative L2."""
     import numpy as np
     import torch
-    try:
-        import oracle
-        r = np.random.default_rng(3).integers(0, n ** 3, size=rows)
-        vol = x[:n ** 3].double().cpu().numpy()
-        ref = oracle.forward_rows(vol, n, r, skew=skew or oracle.CANONICAL_SKEW,
-                                  nthreads=len(os.sched_getaffinity(0)))
-        got = y[torch.from_numpy(r).to(dev)].cpu().numpy()
-        rms = torch.sqrt(torch.mean(torch.abs(y[:n ** 3].to(torch.complex128)) ** 2)).item()
-        err = np.abs(got - ref)
-        return {"rel_l2_est": float(np.sqrt(np.mean(err ** 2)) / rms), "max_err_over_rms": float(err.max() / rms),
-                "rows": rows, "oracle": "FP64 direct definition"}
-    except Exception as exc:  # accuracy is reported, never required
-        return {"error": str(exc)}
+    r = np.random.default_rng(3).integers(0, n ** 3, size=rows)
+    return {"vol": x[:n ** 3].double().cpu().numpy(), "rows": r, "n": n, "skew": skew,
+            "got": y[torch.from_numpy(r).to(dev)].cpu().numpy(),
+            "rms": torch.sqrt(torch.mean(torch.abs(y[:n ** 3].to(torch.complex128)) ** 2)).item()}
+
+
+def evaluate_probes(probes):
+    """CPU leg: the FP64 oracle's rows for each accuracy probe; relative L2
+    estimate and the largest sampled error (over the output RMS)."""
+    import numpy as np
+    import oracle
+    out = {}
+    for name, pr in probes.items():
+        try:
+            ref = oracle.forward_rows(pr["vol"], pr["n"], pr["rows"], skew=pr["skew"] or oracle.CANONICAL_SKEW,
+                                      nthreads=len(os.sched_getaffinity(0)))
+            err = np.abs(pr["got"] - ref)
+            out[name] = {"rel_l2_est": float(np.sqrt(np.mean(err ** 2)) / pr["rms"]),
+                         "max_err_over_rms": float(err.max() / pr["rms"]), "rows": len(pr["rows"]),
+                         "oracle": "FP64 direct definition"}
+        except Exception as exc:  # accuracy is reported, never required
+            out[name] = {"error": str(exc)}
+    return out
 
 
 def _time(fn, steps, warmup):
@@ -344,10 +356,21 @@ def secondary_configs(dev):
     out["skew_n128_b64"] = {"value": pts / (ms * 1e-3) / 1e9, "unit": "Gpoints/s", "ms_per_step": ms,
                             "shift": "(1, 0, 11) / 16", "launches": launches,
                             "step_roofline_frac": pts * 12 / (ms * 1e-3) / (peak * 1e9), "peak_kind": kind,
-                            "kernels_ms": kern, "accuracy": sampled_accuracy(x, y, n, dev, skew=skew),
+                            "kernels_ms": kern, "accuracy_probe": sampled_accuracy(x, y, n, dev, skew=skew),
                             "form": "r32: tiled orbit mixing on staged class cores + register-radix DFT passes"}
     del x, y
     return out
+
+
+def packed_vs_complex(pk, y, n, batch, dev):
+    """Relative L2 between the packed output and the complex output of the
+    same plan re-laid out (primary points keep Re y, the others -Im y)."""
+    import torch
+    idx = torch.arange(n ** 3, device=dev)
+    l, q = (idx // n) % n, idx % n
+    prim = ((2 * l < n) | ((2 * l == n) & (2 * q < n))).repeat(batch)
+    want = torch.where(prim, y.real, -y.imag)
+    return (torch.linalg.vector_norm(pk - want) / torch.linalg.vector_norm(want)).item()
 
 
 def packed_config(plan, x, y, n, batch, args, dev, st):
@@ -371,15 +394,11 @@ def packed_config(plan, x, y, n, batch, args, dev, st):
     # the layout (primary points keep Re y, the others -Im y) applied to the
     # complex output of the same plan
     plan.forward(x, out=y)
-    idx = torch.arange(n ** 3, device=dev)
-    l, q = (idx // n) % n, idx % n
-    prim = ((2 * l < n) | ((2 * l == n) & (2 * q < n))).repeat(batch)
-    want = torch.where(prim, y.real, -y.imag)
-    diff = (torch.linalg.vector_norm(pk - want) / torch.linalg.vector_norm(want)).item()
+    diff = packed_vs_complex(pk, y, n, batch, dev)
     back = torch.empty_like(x)
     plan.inverse_packed(pk, out=back)
     rt = (torch.linalg.vector_norm(back - x) / torch.linalg.vector_norm(x)).item()
-    del back, want, prim
+    del back
     xh = x.cpu().pin_memory()
     pkh = torch.empty(pts, dtype=torch.float32).pin_memory()
     plan.forward_packed_host(xh, pkh)
@@ -416,6 +435,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
     ap.add_argument("--autotune", type=int, default=1, help="run fcc_dct_autotune before timing (1) or not (0)")
+    ap.add_argument("--output", default="complex", choices=["complex", "packed"],
+                    help="forward output: complex64 point values, or the Hermitian-packed reals of real plans")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -441,6 +462,12 @@ def main():
     plan = binding.Plan(n, batch, args.dtype)
     y = torch.empty(pts, dtype=torch.complex64, device=dev)
     st = torch.cuda.current_stream(dev)
+    packed = args.output == "packed"
+    pk = torch.empty(pts, dtype=torch.float32, device=dev) if packed else None
+    step_bytes = 8 if packed else 12   # algorithmic bytes per point of a whole forward step
+
+    def fwd(p=plan):
+        return p.forward_packed(x, out=pk) if packed else p.forward(x, out=y)
 
     def barrier():
         if dist is not None:
@@ -449,7 +476,7 @@ def main():
     # the library's autotuner picks the execution schedule once (untimed)
     sched = plan.autotune(x, y, reps=3)[1] if args.autotune else plan.schedule()
     for _ in range(args.warmup):
-        plan.forward(x, out=y)
+        fwd()
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
@@ -459,7 +486,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        plan.forward(x, out=y)
+        fwd()
     e1.record(st)
     torch.cuda.synchronize()
     barrier()
@@ -473,7 +500,7 @@ def main():
     plan.set_schedule(streams=1)
     plan.profile(True)
     for _ in range(args.steps):
-        plan.forward(x, out=y)
+        fwd()
     torch.cuda.synchronize()
     kern = plan.profile_read()
     plan.profile(False)
@@ -486,7 +513,7 @@ def main():
     paired = args.dtype.startswith("r") and batch >= 2
     if paired:
         algo_bytes = {"mix_tiled_fwd": 8, "mix_tc_fwd": 8, "fft_slab": 8, "fft_pencil": 8, "pair_split": 12,
-                      "fft_pencil_pair": 12}
+                      "fft_pencil_pair": 12, "fft_pencil_pair_packed": 8}
     else:
         algo_bytes = {"mix_tiled_fwd": 12, "fft_slab": 16, "fft_pencil": 16, "orbit_mix_fwd": 12,
                       "fft_axis0": 16, "fft_axis1": 16, "fft_axis2": 16}
@@ -497,15 +524,22 @@ def main():
     peak, peak_kind = _peaks()
     achieved = algo_bytes.get(top_name, 12) * per_launch_pts / (per_launch_ms * 1e-3) / 1e9
     traffic = _traffic(top_name, per_launch_pts) if n == 128 else None
-    step_gbs = 12 * pts / (ms * 1e-3) / 1e9
+    step_gbs = step_bytes * pts / (ms * 1e-3) / 1e9
 
     # accuracy on sampled rows of one volume (outside the timed region)
-    accuracy = sampled_accuracy(x, y, n, dev) if rank == 0 else None
+    probes = {}
+    relayout = None
+    if packed:   # the packed values are the complex output re-laid out
+        plan.forward(x, out=y)
+        relayout = packed_vs_complex(pk, y, n, batch, dev)
+    if rank == 0:
+        probes["headline"] = sampled_accuracy(x, y, n, dev)
 
     # end to end through the C ABI with host buffers
     xh = x.cpu().pin_memory()
-    yh = torch.empty(pts, dtype=torch.complex64).pin_memory()
-    plan.forward_host(xh, yh)
+    yh = torch.empty(pts, dtype=torch.float32 if packed else torch.complex64).pin_memory()
+    fwd_host = plan.forward_packed_host if packed else plan.forward_host
+    fwd_host(xh, yh)
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
@@ -513,7 +547,7 @@ def main():
     barrier()
     e2.record(st)
     for _ in range(ke):
-        plan.forward_host(xh, yh)
+        fwd_host(xh, yh)
     e3.record(st)
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3) / ke
@@ -524,28 +558,43 @@ def main():
         with binding.Plan(n, batch, args.compare) as q:
             q_sched = q.autotune(x, y, reps=3)[1] if args.autotune else q.schedule()
             for _ in range(args.warmup):
-                q.forward(x, out=y)
+                fwd(q)
             torch.cuda.synchronize()
             barrier()
             c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             c0.record(st)
             for _ in range(args.steps):
-                q.forward(x, out=y)
+                fwd(q)
             c1.record(st)
             torch.cuda.synchronize()
             ms_c = c0.elapsed_time(c1) / args.steps
-            acc_c = sampled_accuracy(x, y, n, dev) if rank == 0 else None
+            if packed:
+                q.forward(x, out=y)
+            if rank == 0:
+                probes["compare"] = sampled_accuracy(x, y, n, dev)
             compare = {"form": args.compare, "value": world * pts / (ms_c * 1e-3) / 1e9, "unit": UNIT,
-                       "ms_per_step": ms_c, "accuracy": acc_c, "schedule": q_sched}
+                       "ms_per_step": ms_c, "schedule": q_sched}
 
     extra = None
     if rank == 0 and not args.no_extra and n == 128 and batch == 64:
         extra = secondary_configs(dev)
-        extra["packed_n%d_b%d" % (n, batch)] = packed_config(plan, x, y, n, batch, args, dev, st)
+        if not packed:
+            extra["packed_n%d_b%d" % (n, batch)] = packed_config(plan, x, y, n, batch, args, dev, st)
 
+    # the CPU leg (rank 0, one GPU): the oracle timed on the host cores, and the
+    # oracle's rows for the accuracy probes taken above
     cpu = None
+    if extra and "skew_n128_b64" in extra:
+        probes["skew"] = extra["skew_n128_b64"].pop("accuracy_probe")
+    acc = {k: {"skipped": "oracle leg not run (--no-cpu-baseline or N > 1)"} for k in probes}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
+        acc = evaluate_probes(probes)
+    if compare is not None and "compare" in acc:
+        compare["accuracy"] = acc["compare"]
+    if extra and "skew" in acc:
+        extra["skew_n128_b64"]["accuracy"] = acc["skew"]
+    accuracy = acc.get("headline")
 
     if rank == 0:
         line = {
@@ -555,17 +604,19 @@ def main():
             "dtype": {"r32": "f32", "r32_bf16x3": "bf16x3/f32", "r32_tf32x3": "tf32x3/f32",
                       "r32_bf16x6": "bf16x6/f32"}.get(args.dtype, args.dtype),
             "data": "synthetic CT-like phantoms (10-30 random ellipsoids, densities U[0,1], +N(0,1e-3^2)), seeded",
-            "config": {"workload": "FCC-DCT forward y = DCT_n x, order n=%d, batch %d, FP32 real -> complex64, "
-                                   "%s form" % (n, batch, FORM_NAMES.get(args.dtype, args.dtype)),
+            "config": {"workload": "FCC-DCT forward y = DCT_n x, order n=%d, batch %d, FP32 real -> %s, "
+                                   "%s form" % (n, batch, "Hermitian-packed FP32 reals" if packed else "complex64",
+                                                FORM_NAMES.get(args.dtype, args.dtype)),
+                       "output": args.output, "packed_equals_complex_relaid": relayout,
                        "order": n, "batch": batch, "points_per_step": pts, "form": args.dtype,
                        "schedule": sched, "autotuned": bool(args.autotune),
                        "l2": "inputs %.0f MB + outputs %.0f MB per step exceed the 126 MB L2"
-                             % (pts * 4 / 1e6, pts * 8 / 1e6)},
+                             % (pts * 4 / 1e6, pts * (step_bytes - 4) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_point": algo_bytes.get(top_name, 12)},
-            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": 12},
+            "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": step_bytes},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "kernels": {k: {"launches_per_step": v[1] / args.steps, "ms_per_launch": v[0] / v[1],
                             "achieved_gbs": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9,
@@ -573,8 +624,8 @@ def main():
                         for k, v in kern.items()},
             "kernel_timing": "CUDA events around each launch, one internal stream (each kernel alone)",
             "e2e": {"value": world * pts / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
-                    "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 8)},
-            "gpu_launches": plan.launches(0) * args.steps,
+                    "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * yh.element_size())},
+            "gpu_launches": plan.launches(3 if packed else 0) * args.steps,
             "clocks": ck,
             "accuracy": accuracy,
             "compare": compare,
