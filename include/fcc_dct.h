@@ -268,6 +268,13 @@ fcc_status fcc_dct_test_wait_timeout(fcc_plan* plan, int enable);
  *                                  run of equal orders
  *   FCC_SCHED_TC_BLOCKS  0..4      tensor-core mixing: blocks per SM in the
  *                                  grid (0 = as many as can be resident)
+ *   FCC_SCHED_TC_FOLD    0, 1      tensor-core forward, orders with register
+ *                                  DFT passes: 1 (default) = the mixing writes
+ *                                  its sums without the row phase and 1/24
+ *                                  (the slot's 8th-root wrap factor is in the
+ *                                  core) and the slab / pencil passes multiply
+ *                                  their inputs by the separable rest; 0 = the
+ *                                  mixing applies the row phase
  * set_schedule returns FCC_ERR_INVALID_ARG for an unknown key or a value out
  * of range; get_schedule returns the current value, or -1 on a bad argument.
  */
@@ -275,7 +282,8 @@ typedef enum {
     FCC_SCHED_CHUNK_MB = 0,
     FCC_SCHED_STREAMS = 1,
     FCC_SCHED_RAGGED = 2,
-    FCC_SCHED_TC_BLOCKS = 3
+    FCC_SCHED_TC_BLOCKS = 3,
+    FCC_SCHED_TC_FOLD = 4
 } fcc_sched_key;
 fcc_status fcc_dct_set_schedule(fcc_plan* plan, int key, int value);
 int fcc_dct_get_schedule(const fcc_plan* plan, int key);

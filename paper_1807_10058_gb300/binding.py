@@ -27,7 +27,7 @@ EXPORTS = [
 ]
 
 # execution-schedule keys (fcc_sched_key)
-SCHED = {"chunk_mb": 0, "streams": 1, "ragged": 2, "tc_blocks": 3}
+SCHED = {"chunk_mb": 0, "streams": 1, "ragged": 2, "tc_blocks": 3, "tc_fold": 4}
 
 _LIB = None
 

@@ -83,12 +83,21 @@ struct OrderTables {
     int tc_nbgroups = 0;
     // inverse / adjoint blocks of every class, three BF16 terms each (six-product form)
     void* tc_inv_images[2] = {nullptr, nullptr};
+    // phase-free forward (canonical shift): core images with the wrap factor
+    // w_8^{m_g.v} in row g (free class, then every class), and the input
+    // modulations of the slab pass (w_{8n}^{v3 c}) and of the pencil pass
+    // (w_{8n}^{v1 k} / 24); null where the row phase stays in the mixing
+    void* tc_core_image_f = nullptr;
+    void* tc_core_images_f = nullptr;
+    void* pre_slab = nullptr;
+    void* pre_pencil = nullptr;
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
 };
 
 constexpr int kMaxStreams = 4;
+constexpr double kPi = 3.14159265358979323846;
 
 }  // namespace
 
@@ -124,6 +133,7 @@ struct fcc_plan {
     bool ragged_fast = true;         // ragged FP32 forward: per-order launches over offset tables
     int ragged_mode = 0;             // FCC_SCHED_RAGGED: 0 per-order launches, 1 one persistent launch, 2 per run of volumes
     int tc_blocks = 0;               // FCC_SCHED_TC_BLOCKS: tensor-core mixing blocks per SM in the grid (0 = resident maximum)
+    int tc_fold = 1;                 // FCC_SCHED_TC_FOLD: 1 = row phase applied by the DFT passes (phase-free mixing)
     int wait_test = 0;               // fcc_dct_test_wait_timeout
     int scratch_streams = 1;         // internal streams the inverse / adjoint workspace was sized for
     int num_sms = 1;
@@ -233,6 +243,37 @@ fcc_status build_tables(fcc_plan* p, int n, OrderTables& t) {
                                                    : build_tc_core_image<1>(hp.classes[hp.free_class].fwd.data(), img);
         if (!ok) return FCC_ERR_UNSUPPORTED;
         if ((s = upload(p, &t.tc_core_image, img.data(), img.size()))) return s;
+        // phase-free form: R_g = w_{dn}^{kappa_g.v} w_d^{m_g.v}; the class's
+        // wrap factor goes into row g of its core, the rest into the DFT passes
+        const bool fold = sizeof(T) == 4 && hp.d == 8 && hp.v[1] == 0;
+        auto folded = [&](const OrbitClass& oc, std::vector<unsigned char>& out) -> bool {
+            std::vector<cd> f(oc.fwd);
+            for (int g = 0; g < 24; ++g) {
+                const int e = oc.wrap[g][0] * hp.v[0] + oc.wrap[g][1] * hp.v[1] + oc.wrap[g][2] * hp.v[2];
+                const cd w = std::polar(1.0, 2.0 * kPi * (double)(((e % hp.d) + hp.d) % hp.d) / hp.d);
+                for (int h = 0; h < 24; ++h) f[g * 24 + h] *= w;
+            }
+            return is_bf16(p->dtype) ? build_tc_core_image<0>(f.data(), out) : build_tc_core_image<1>(f.data(), out);
+        };
+        if (fold) {
+            std::vector<unsigned char> fimg, fall, one;
+            if (!folded(hp.classes[hp.free_class], fimg)) return FCC_ERR_UNSUPPORTED;
+            for (size_t c = 0; c < hp.classes.size(); ++c) {
+                if (!folded(hp.classes[c], one)) return FCC_ERR_UNSUPPORTED;
+                fall.insert(fall.end(), one.begin(), one.end());
+            }
+            std::vector<cd> ps(n), pp(n);
+            const int M = hp.d * n;
+            for (int c = 0; c < n; ++c) {
+                ps[c] = std::polar(1.0, 2.0 * kPi * (double)(((int64_t)hp.v[2] * c) % M) / M);
+                pp[c] = std::polar(1.0 / 24.0, 2.0 * kPi * (double)(((int64_t)hp.v[0] * c) % M) / M);
+            }
+            auto psv = to_pairs<float>(ps), ppv = to_pairs<float>(pp);
+            if ((s = upload(p, &t.tc_core_image_f, fimg.data(), fimg.size()))) return s;
+            if ((s = upload(p, &t.tc_core_images_f, fall.data(), fall.size()))) return s;
+            if ((s = upload(p, &t.pre_slab, psv.data(), psv.size() * 4))) return s;
+            if ((s = upload(p, &t.pre_pencil, ppv.data(), ppv.size() * 4))) return s;
+        }
         const int ntl = (int)hp.tile_off.size() - 1;
         std::vector<uint32_t> r32((size_t)std::max(1, ntl) * 32, 0xffffffffu);
         for (int tl = 0; tl < ntl; ++tl)
@@ -726,8 +767,29 @@ fcc_status launch_pair(bool split, int n, const float* in, float* out, int64_t n
 // Forward 3-D DFT of `np` paired chunks (Y of pair p at volume 2p of y) and
 // the split into D x1, D x2: the fast path fuses the split into the last
 // (pencil) pass; otherwise DFT passes then the split kernel.
-fcc_status dft3_split_pairs(const OrderTables& t, float* y, int64_t np, cudaStream_t st) {
+// fold: the inputs are the phase-free sums of launch_mix_tc_pairs(..., fold);
+// the slab and pencil passes apply the row phase's grid factor and 1/24.
+bool fold_ok(const OrderTables& t, const float* y) {
+    return t.tc_core_image_f && t.pre_slab && has_fast_fft(t.n) && ((uintptr_t)y & 15u) == 0;
+}
+
+fcc_status dft3_split_pairs(const OrderTables& t, float* y, int64_t np, cudaStream_t st, bool fold = false) {
     const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    if (fold) {
+        if (!fold_ok(t, y)) return FCC_ERR_UNSUPPORTED;
+        const float2* tw = (const float2*)t.tw;
+        {
+            ProfScope ps("fft_slab", st);
+            if (launch_fast_slab_pre(t.n, (const float2*)y, (float2*)y, np, tw, (const float2*)t.pre_slab, 2 * n3, st) !=
+                cudaSuccess)
+                return FCC_ERR_CUDA;
+        }
+        ProfScope ps("fft_pencil_pair", st);
+        return launch_fast_pencil_pair(t.n, (const float2*)y, (float2*)y, np, tw, 2 * n3, st, false,
+                                       (const float2*)t.pre_pencil) == cudaSuccess
+                   ? FCC_OK
+                   : FCC_ERR_CUDA;
+    }
     if (has_fast_fft(t.n) && ((uintptr_t)y & 15u) == 0) {
         const float2* tw = (const float2*)t.tw;
         fcc_status s = fast_fft(t.n, true, +1, (const float2*)y, (float2*)y, np, tw, 2 * n3, st);
@@ -760,8 +822,10 @@ fcc_status merge_dft3_pairs(const OrderTables& t, const float* y, float* ws, int
 
 // Forward mixing of `np` pairs of real volumes with the orbit core on the
 // tensor cores for the free tiles, the SIMT kernel for the boundary tiles.
+// fold: the phase-free form (pair with dft3_split_pairs(..., fold)): the
+// mixing writes the sums without row phase and 1/24, the DFT passes modulate.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool fold = false) {
     TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
     const bool bf16 = is_bf16(p->dtype);
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
@@ -770,26 +834,39 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
     if (!attr.done()) {
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<0>::smem);
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<1>::smem);
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcLayout<0>::smem);
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcLayout<1>::smem);
         attr.mark();
     }
+    if (fold && !(t.tc_core_image_f && t.tc_core_image)) return FCC_ERR_UNSUPPORTED;
     for (int64_t v0 = 0; v0 < np; v0 += 65535) {
         const int64_t nv = std::min<int64_t>(65535, np - v0);
         const float* src = in + v0 * a.n3 * 2;
         float* dst = out + v0 * a.n3 * 4;
         if (t.free_tiles > 0 && t.tc_core_image) {
             const int ngroups = (t.free_tiles + 3) / 4 + t.tc_nbgroups;
-            const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups, (const uint4*)t.tc_core_images, t.tc_off, t.canon_mask};
+            const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups,
+                                    (const uint4*)(fold ? t.tc_core_images_f : t.tc_core_images), t.tc_off, t.canon_mask};
             const int lim = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
             const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, lim) : lim;
             const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);
-            if (bf16)
-                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
+            const uint4* ci = (const uint4*)(fold ? t.tc_core_image_f : t.tc_core_image);
+            if (bf16 && fold)
+                mix_tc_fwd_pair_kernel<0, false><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                                 p->d_status, bnd, p->wait_test);
+            else if (bf16)
+                mix_tc_fwd_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                          p->d_status, bnd, p->wait_test);
+            else if (fold)
+                mix_tc_fwd_pair_kernel<1, false><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                                 p->d_status, bnd, p->wait_test);
             else
-                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32,
-                                                                          (const uint4*)t.tc_core_image, p->d_status, bnd, p->wait_test);
+                mix_tc_fwd_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                          p->d_status, bnd, p->wait_test);
         }
         if (!t.tc_core_image) {   // no free orbits at this order: every tile is a boundary tile
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
@@ -868,15 +945,14 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             const float* x = in + 2 * p0 * n3;
             float* y = out + 2 * p0 * n3 * 2;
             const int part = split_boundary ? 1 : 0;
-            if (tc_all) {
-                s = launch_mix_tc_pairs(p, t, x, y, np, ss);
-            } else if (is_tc(p->dtype)) {
-                s = launch_mix_tc_pairs(p, t, x, y, np, ss);
+            const bool fold = tc_all && p->tc_fold && fold_ok(t, y);
+            if (is_tc(p->dtype)) {
+                s = launch_mix_tc_pairs(p, t, x, y, np, ss, fold);
             } else {
                 s = launch_mix_tiled(t, MODE_FWD, true, false, x, y, np, 1.f, ss, true, part);
             }
             if (!s && split_boundary && cudaStreamWaitEvent(ss, p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
-            if (!s) s = dft3_split_pairs(t, y, np, ss);
+            if (!s) s = dft3_split_pairs(t, y, np, ss, fold);
         } else {
             float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
             const float* y = in + 2 * p0 * n3 * 2;
@@ -1172,12 +1248,21 @@ fcc_status run_pairs_packed(fcc_plan* p, int which, const OrderTables& t, const 
         const float* src = in + 2 * p0 * n3;
         float* dst = out + 2 * p0 * n3;
         if (which == 0) {
-            s = tc ? launch_mix_tc_pairs(p, t, src, ws, np, ss)
+            const bool fold = tc_all && p->tc_fold && fold_ok(t, ws);
+            s = tc ? launch_mix_tc_pairs(p, t, src, ws, np, ss, fold)
                    : launch_mix_tiled(t, MODE_FWD, true, false, src, ws, np, 1.f, ss, true);
-            if (!s) s = fast_fft(t.n, true, +1, (const float2*)ws, (float2*)ws, np, tw, 2 * n3, ss);
+            if (!s && fold) {
+                ProfScope ps("fft_slab", ss);
+                if (launch_fast_slab_pre(t.n, (const float2*)ws, (float2*)ws, np, tw, (const float2*)t.pre_slab, 2 * n3, ss) !=
+                    cudaSuccess)
+                    s = FCC_ERR_CUDA;
+            } else if (!s) {
+                s = fast_fft(t.n, true, +1, (const float2*)ws, (float2*)ws, np, tw, 2 * n3, ss);
+            }
             if (!s) {
                 ProfScope ps("fft_pencil_pair_packed", ss);
-                if (launch_fast_pencil_pair(t.n, (const float2*)ws, (float2*)dst, np, tw, 2 * n3, ss, true) != cudaSuccess)
+                if (launch_fast_pencil_pair(t.n, (const float2*)ws, (float2*)dst, np, tw, 2 * n3, ss, true,
+                                            fold ? (const float2*)t.pre_pencil : nullptr) != cudaSuccess)
                     s = FCC_ERR_CUDA;
             }
         } else {
@@ -1542,6 +1627,10 @@ fcc_status fcc_dct_set_schedule(fcc_plan* p, int key, int value) {
             if (value < 0 || value > 4) return fail(FCC_ERR_INVALID_ARG);
             p->tc_blocks = value;
             return FCC_OK;
+        case FCC_SCHED_TC_FOLD:
+            if (value < 0 || value > 1) return fail(FCC_ERR_INVALID_ARG);
+            p->tc_fold = value;
+            return FCC_OK;
         default:
             return fail(FCC_ERR_INVALID_ARG);
     }
@@ -1554,6 +1643,7 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
         case FCC_SCHED_STREAMS: return p->nstreams;
         case FCC_SCHED_RAGGED: return p->ragged_mode;
         case FCC_SCHED_TC_BLOCKS: return p->tc_blocks;
+        case FCC_SCHED_TC_FOLD: return p->tc_fold;
         default: return -1;
     }
 }
@@ -1561,17 +1651,17 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
 fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream, int reps, float* best_ms) {
     if (!p || !in || !out || reps < 1 || reps > 100) return fail(FCC_ERR_INVALID_ARG);
     cudaStream_t st = (cudaStream_t)stream;
-    struct Cand { int chunk_mb, streams, ragged, tc; };
+    struct Cand { int chunk_mb, streams, ragged, tc, fold; };
     std::vector<Cand> cands;
-    const int tc0 = p->tc_blocks;
+    const int tc0 = p->tc_blocks, f0 = p->tc_fold;
     if (!p->uniform) {
         const bool fast = !is_double(p->dtype) && ragged_fast_ok(p, 0);
-        for (int ns = 1; ns <= kMaxStreams && fast; ++ns) cands.push_back({32, ns, 0, tc0});
-        if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0});
-        cands.push_back({32, 2, 2, tc0});
+        for (int ns = 1; ns <= kMaxStreams && fast; ++ns) cands.push_back({32, ns, 0, tc0, f0});
+        if (fast && ragged_persistent_ok(p)) cands.push_back({32, 2, 1, tc0, f0});
+        cands.push_back({32, 2, 2, tc0, f0});
     } else {
         for (int mb : {8, 16, 32, 64})
-            for (int ns = 1; ns <= kMaxStreams; ++ns) cands.push_back({mb, ns, 0, tc0});
+            for (int ns = 1; ns <= kMaxStreams; ++ns) cands.push_back({mb, ns, 0, tc0, f0});
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1579,12 +1669,13 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
         cudaGetLastError();
         return fail(FCC_ERR_CUDA);
     }
-    const Cand saved = {(int)(p->chunk_bytes >> 20), p->nstreams, p->ragged_mode, p->tc_blocks};
+    const Cand saved = {(int)(p->chunk_bytes >> 20), p->nstreams, p->ragged_mode, p->tc_blocks, p->tc_fold};
     auto apply = [&](const Cand& c) {
         p->chunk_bytes = (int64_t)c.chunk_mb << 20;
         p->nstreams = c.streams;
         p->ragged_mode = c.ragged;
         p->tc_blocks = c.tc;
+        p->tc_fold = c.fold;
     };
     auto time_it = [&](const Cand& c, float& ms) -> bool {
         apply(c);
@@ -1616,8 +1707,18 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
             best = c;
         }
     }
-    // tensor-core forms: then the grid of the mixing kernel
+    // tensor-core forms: then where the row phase is applied, and the grid of
+    // the mixing kernel
     if (p->uniform && is_tc(p->dtype) && best_t >= 0.f) {
+        {
+            Cand c = best;
+            c.fold = 1 - c.fold;
+            float ms = 0.f;
+            if (time_it(c, ms) && ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
         for (int tcb : {2, 3, 4}) {
             Cand c = best;
             c.tc = tcb;

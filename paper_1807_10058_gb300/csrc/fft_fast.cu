@@ -37,22 +37,43 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
 
 template <int N>
 cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const float2* tw, int64_t vstride,
-                          cudaStream_t st, bool packed) {
+                          cudaStream_t st, bool packed, const float2* pre) {
     using L = FastLayout<N>;
     if (vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
     // packed: 4-byte stores to a separate output (the complex input is not overwritten in place)
     if (packed && (((uintptr_t)out & 3u) != 0 || (const void*)in == (const void*)out)) return cudaErrorInvalidValue;
+    const size_t sm = L::pencil_smem, smp = L::pencil_smem + N * sizeof(float2);
     static DeviceOnce attr;
     if (!attr.done()) {
-        cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
-        cudaFuncSetAttribute(fft_pencil_pair_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L::pencil_smem);
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        cudaFuncSetAttribute(fft_pencil_pair_kernel<N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
         attr.mark();
     }
     const int64_t g = npairs * (N / 2 + 1) * PairLayout<N>::CBLK;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (packed) fft_pencil_pair_kernel<N, true><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
-    else fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, vstride);
+    if (packed && pre) fft_pencil_pair_kernel<N, true, true><<<(unsigned)g, kFastThreads, smp, st>>>(in, out, tw, vstride, pre);
+    else if (packed) fft_pencil_pair_kernel<N, true><<<(unsigned)g, kFastThreads, sm, st>>>(in, out, tw, vstride);
+    else if (pre) fft_pencil_pair_kernel<N, false, true><<<(unsigned)g, kFastThreads, smp, st>>>(in, out, tw, vstride, pre);
+    else fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, sm, st>>>(in, out, tw, vstride);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_slab_pre_n(const float2* in, float2* out, int64_t nvol, const float2* tw, const float2* pre,
+                              int64_t vstride, cudaStream_t st) {
+    using L = FastLayout<N>;
+    if (((((uintptr_t)in) | ((uintptr_t)out)) & 15u) != 0 || vstride % 2 != 0 || !pre) return cudaErrorInvalidValue;
+    const size_t smp = L::slab_smem + N * sizeof(float2);
+    static DeviceOnce attr;
+    if (!attr.done()) {
+        cudaFuncSetAttribute(fft_slab_kernel<N, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        attr.mark();
+    }
+    const int64_t g = nvol * N;
+    if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+    fft_slab_kernel<N, 1, true><<<(unsigned)g, L::SLAB_THREADS, smp, st>>>(in, out, tw, vstride, nullptr, pre);
     return cudaGetLastError();
 }
 
@@ -92,9 +113,21 @@ cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64
 }
 
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                    int64_t vstride, cudaStream_t st, bool packed) {
+                                    int64_t vstride, cudaStream_t st, bool packed, const float2* pre) {
     switch (n) {
-#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st, packed);
+#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st, packed, pre);
+        FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
+        FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
+#undef FCC_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fast_slab_pre(int n, const float2* in, float2* out, int64_t nvol, const float2* tw,
+                                 const float2* pre, int64_t vstride, cudaStream_t st) {
+    switch (n) {
+#define FCC_CASE(NN) case NN: return launch_slab_pre_n<NN>(in, out, nvol, tw, pre, vstride, st);
         FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
         FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
 #undef FCC_CASE

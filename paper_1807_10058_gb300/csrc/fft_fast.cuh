@@ -198,18 +198,32 @@ constexpr size_t slab_smem_for(int sw) {
 }
 
 // DFT along the two fast axes of the n x n slab starting at `base` (complex
-// values), by a block of SW warps; in and out may alias.
-template <int N, int S, int SW>
+// values), by a block of SW warps; in and out may alias.  PRE: every input
+// value is first multiplied by preg[c], c its index along the fastest axis
+// (a separable modulation of the input; N more complex values of shared
+// memory).
+template <int N, int S, int SW, bool PRE = false>
 __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, const float2* __restrict__ twg,
-                                              int64_t base, unsigned char* smem_raw) {
+                                              int64_t base, unsigned char* smem_raw,
+                                              const float2* __restrict__ preg = nullptr) {
     using L = FastLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, LD = L::LD;
     float2* slab = reinterpret_cast<float2*>(smem_raw);
     float2* exall = slab + N * LD;
     float2* tw = exall + SW * L::EXW;
+    float2* pre = tw + N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < N; t += 32 * SW) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < N; t += 32 * SW) {
+        tw[t] = twg[t];
+        if (PRE) pre[t] = preg[t];
+    }
     __syncthreads();
+    // input value at fast index c, modulated when PRE
+    auto modulate = [&](float2 t, int c) -> float2 {
+        if (!PRE) return t;
+        const float2 w = pre[c];
+        return make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
+    };
 
     // rows (fastest axis)
     {
@@ -227,7 +241,7 @@ __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, con
                 const float2* src = in + base + (int64_t)r * N + j;
 #pragma unroll
                 for (int m = 0; m < R1; ++m) {
-                    const float2 t = act ? src[G * m] : make_float2(0.f, 0.f);
+                    const float2 t = modulate(act ? src[G * m] : make_float2(0.f, 0.f), j + G * m);
                     vr[rd][m] = t.x;
                     vi[rd][m] = t.y;
                 }
@@ -263,7 +277,7 @@ __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, con
                 const float2* src = in + base + (int64_t)r * N + j;
 #pragma unroll
                 for (int m = 0; m < R1; ++m) {
-                    const float2 t = act ? src[G * m] : make_float2(0.f, 0.f);
+                    const float2 t = modulate(act ? src[G * m] : make_float2(0.f, 0.f), j + G * m);
                     vr[m] = t.x;
                     vi[m] = t.y;
                 }
@@ -321,13 +335,16 @@ __device__ __forceinline__ void fft_slab_body(const float2* in, float2* out, con
 }
 
 // grid.x = number of slabs (volumes * N); volume v starts at voff[v] (or
-// v * vstride) complex values; in and out may alias.
-template <int N, int S>
+// v * vstride) complex values; in and out may alias.  PRE: inputs modulated
+// by pre[c] along the fastest axis (dynamic shared memory slab_smem + N
+// complex values).
+template <int N, int S, bool PRE = false>
 __global__ void __launch_bounds__(FastLayout<N>::SLAB_THREADS, 1)
-fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff) {
+fft_slab_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride, const int64_t* voff,
+                const float2* __restrict__ pre = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t base = vol_base(voff, blockIdx.x / N, vstride) + (int64_t)(blockIdx.x % N) * N * N;
-    fft_slab_body<N, S, FastLayout<N>::SW>(in, out, twg, base, smem_raw);
+    fft_slab_body<N, S, FastLayout<N>::SW, PRE>(in, out, twg, base, smem_raw, pre);
 }
 
 // NP adjacent pencils (columns c, c+1) per thread.  grid.x = volumes * N (b)
@@ -445,9 +462,12 @@ struct PairLayout {
     static constexpr int CBLK = (N + CPB2 - 1) / CPB2;
 };
 
-template <int N, bool PACKED = false>
+// PRE: the pencil's inputs are first multiplied by pre[k], k their index
+// along the slow axis (dynamic shared memory pencil_smem + N complex values).
+template <int N, bool PACKED = false, bool PRE = false>
 __global__ void __launch_bounds__(kFastThreads)
-fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride) {
+fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride,
+                       const float2* __restrict__ preg = nullptr) {
     using L = FastLayout<N>;
     using P = PairLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
@@ -456,8 +476,12 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* exall = reinterpret_cast<float2*>(smem_raw);
     float2* tw = exall + kFastWarps * L::EXW;
+    float2* pre = tw + N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < N; t += kFastThreads) tw[t] = twg[t];
+    for (int t = threadIdx.x; t < N; t += kFastThreads) {
+        tw[t] = twg[t];
+        if (PRE) pre[t] = preg[t];
+    }
     __syncthreads();
     const int64_t blk = blockIdx.x;
     const int64_t pr = blk / (ROWS * P::CBLK);
@@ -482,8 +506,14 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
 #pragma unroll
         for (int m = 0; m < R1; ++m) {
             const float2 t = act ? in[base + (int64_t)(j + G * m) * NN] : make_float2(0.f, 0.f);
-            vr[m] = t.x;
-            vi[m] = t.y;
+            if (PRE) {
+                const float2 w = pre[j + G * m];
+                vr[m] = t.x * w.x - t.y * w.y;
+                vi[m] = t.x * w.y + t.y * w.x;
+            } else {
+                vr[m] = t.x;
+                vi[m] = t.y;
+            }
         }
         pencil_stage1<N, 1>(vr, vi, j, ex, tw);
         __syncwarp();
@@ -663,8 +693,13 @@ cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2
 cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
                                      cudaStream_t st, bool packed = false);
 // forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
-// (packed: out receives Hermitian-packed real volumes, pair p at p * 2 n^3 floats)
+// (packed: out receives Hermitian-packed real volumes, pair p at p * 2 n^3 floats;
+// pre: n complex factors the inputs are multiplied by along the slow axis, or null)
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                    int64_t vstride, cudaStream_t st, bool packed = false);
+                                    int64_t vstride, cudaStream_t st, bool packed = false,
+                                    const float2* pre = nullptr);
+// forward slab pass (+ sign) with the inputs multiplied by pre[c] along the fastest axis
+cudaError_t launch_fast_slab_pre(int n, const float2* in, float2* out, int64_t nvol, const float2* tw,
+                                 const float2* pre, int64_t vstride, cudaStream_t st);
 
 }  // namespace fcc

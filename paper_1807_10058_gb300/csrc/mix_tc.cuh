@@ -148,7 +148,10 @@ __device__ __forceinline__ void gather_half(const TiledMixArgs& a, const float* 
 // 4H + 47 of lane trow, A1 + A2 / sqrt 2, row phase R_g / 24, scatter.
 // off, cmask: wrap offsets and canonical slots of the tile's class (a
 // boundary class writes each of its distinct points once).
-template <int H, bool BND>
+// PH = false: no row phase and no 1/24 (the caller's core image carries the
+// wrap factor of R_g and the DFT passes apply the rest, see
+// mix_tc_fwd_pair_kernel).
+template <int H, bool BND, bool PH = true>
 __device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t trow, uint32_t rep, const int* off,
                                               uint32_t cmask, float2* out, int64_t pb, int M8) {
     const float rs2 = 0.70710678118654752440f;
@@ -168,12 +171,14 @@ __device__ __forceinline__ void epilogue_half(const TiledMixArgs& a, uint32_t tr
                 const int g = H + 4 * c + s4;
                 const float re = fmaf(__uint_as_float(v[4 * s4 + 2]), rs2, __uint_as_float(v[4 * s4]));
                 const float im = fmaf(__uint_as_float(v[4 * s4 + 3]), rs2, __uint_as_float(v[4 * s4 + 1]));
-                int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
-                q = q < 0 ? q + M8 : q;
                 const int gi = rep_dot(rep, a.lin[g][0], a.lin[g][1], a.lin[g][2]) + (BND ? __ldg(off + g) : a.lin[g][3]);
-                if (!BND || ((cmask >> g) & 1u)) {
+                if (PH && (!BND || ((cmask >> g) & 1u))) {
+                    int q = rep_dot(rep, c_u[g][0], c_u[g][1], c_u[g][2]);
+                    q = q < 0 ? q + M8 : q;
                     const float2 R = __ldg(a.phase + q);
                     out[pb + gi] = make_float2(sc * (R.x * re - R.y * im), sc * (R.x * im + R.y * re));
+                } else if (!PH && (!BND || ((cmask >> g) & 1u))) {
+                    out[pb + gi] = make_float2(re, im);
                 }
             });
         }
@@ -198,7 +203,16 @@ struct TcBoundary {
 // status: set to 1 if a tensor-core completion wait exceeded its bound.
 // wait_test: issue no MMA and no completion signal, so that the (shortened)
 // wait runs out -- the test of the timeout path; nothing is written then.
-template <int KIND>
+//
+// PH = false (canonical shift, orders with register DFT passes): with
+// W_g kO = kappa_g + n m_g the row phase factors as
+// R_g = w_{8n}^{kappa_g . v} w_8^{m_g . v}.  The second factor depends only on
+// the slot and the class's wrap vectors: the core images passed in carry it
+// in their rows (still 8th roots of unity, so the split stays exact).  The
+// first factor and the 1/24 are a separable modulation of Z that the DFT
+// passes apply to their inputs (fft_slab_kernel / fft_pencil_pair_kernel with
+// PRE), so the kernel writes sum_h w_8^{m_g . v} E[g][h] x[kappa_h] as is.
+template <int KIND, bool PH = true>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
                        const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status,
@@ -341,13 +355,13 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
         if (ok) {   // warp-uniform: tcgen05.ld is executed by whole warps
             float2* o2 = reinterpret_cast<float2*>(out);
             if (cls == a.free_class) {
-                if (half == 0) epilogue_half<0, false>(a, trow, rep, nullptr, 0u, o2, pb, M8);
-                else epilogue_half<12, false>(a, trow, rep, nullptr, 0u, o2, pb, M8);
+                if (half == 0) epilogue_half<0, false, PH>(a, trow, rep, nullptr, 0u, o2, pb, M8);
+                else epilogue_half<12, false, PH>(a, trow, rep, nullptr, 0u, o2, pb, M8);
             } else {
                 const int* off = bnd.off + 24 * cls;
                 const uint32_t cm = __ldg(bnd.canon_mask + cls);
-                if (half == 0) epilogue_half<0, true>(a, trow, rep, off, cm, o2, pb, M8);
-                else epilogue_half<12, true>(a, trow, rep, off, cm, o2, pb, M8);
+                if (half == 0) epilogue_half<0, true, PH>(a, trow, rep, off, cm, o2, pb, M8);
+                else epilogue_half<12, true, PH>(a, trow, rep, off, cm, o2, pb, M8);
             }
         }
         // TMEM reads complete before the next tile's MMAs (issued after the next barrier)

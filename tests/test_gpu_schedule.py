@@ -80,12 +80,12 @@ def test_persistent_ragged_launch_in_cuda_graph():
 def test_schedule_arguments_are_checked():
     with binding.Plan(32, 2, "r32") as p:
         L = binding.lib()
-        for key, bad in ((0, 0), (0, 2000), (1, 0), (1, 5), (2, 3), (3, 5), (4, 0), (9, 1)):
+        for key, bad in ((0, 0), (0, 2000), (1, 0), (1, 5), (2, 3), (3, 5), (4, 2), (4, -1), (9, 1)):
             assert L.fcc_dct_set_schedule(p.handle, key, bad) == binding.FCC_ERR_INVALID_ARG
         # one persistent launch is for ragged plans only
         assert L.fcc_dct_set_schedule(p.handle, 2, 1) == binding.FCC_ERR_UNSUPPORTED
         assert L.fcc_dct_get_schedule(p.handle, 9) == -1
-        assert p.schedule() == {"chunk_mb": 32, "streams": 2, "ragged": 0, "tc_blocks": 0}
+        assert p.schedule() == {"chunk_mb": 32, "streams": 2, "ragged": 0, "tc_blocks": 0, "tc_fold": 1}
 
 
 @pytest.mark.parametrize("dtype", ["r32", "r32_bf16x3"])
@@ -172,3 +172,27 @@ def test_tensor_core_wait_timeout_is_reported_and_the_context_survives():
         assert torch.equal(y, ref)
     with binding.Plan(n, batch, "r32") as q:
         assert L.fcc_dct_test_wait_timeout(q.handle, 1) == binding.FCC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32_tf32x3"])
+@pytest.mark.parametrize("n,batch", [(128, 4), (64, 5), (24, 3), (8, 2)])
+def test_row_phase_in_dft_passes_matches_mixing_epilogue(dtype, n, batch):
+    """FCC_SCHED_TC_FOLD: the row phase applied by the slab / pencil passes
+    (default) or in the mixing epilogue gives the same transform to FP32
+    rounding, complex and packed, with the same launch count."""
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(n)
+    x = torch.rand(batch * n ** 3, generator=gen, device=DEV, dtype=torch.float32) * 2 - 1
+    with binding.Plan(n, batch, dtype) as p:
+        assert p.schedule()["tc_fold"] == 1
+        y1 = p.forward(x)
+        k1 = p.forward_packed(x)
+        l1 = (p.launches(0), p.launches(3))
+        p.set_schedule(tc_fold=0)
+        y0 = p.forward(x)
+        k0 = p.forward_packed(x)
+        assert (p.launches(0), p.launches(3)) == l1
+        p.check()
+    d = (torch.linalg.vector_norm(y1 - y0) / torch.linalg.vector_norm(y0)).item()
+    dk = (torch.linalg.vector_norm(k1 - k0) / torch.linalg.vector_norm(k0)).item()
+    assert d < 5e-7 and dk < 5e-7, (d, dk)

@@ -148,3 +148,33 @@ def test_equal_shifts_give_equal_cores():
     assert np.array_equal(a["reps"], b["reps"]) and np.array_equal(a["cls"], b["cls"])
     for m in ("fwd", "inv", "adj"):
         assert np.abs(a[m] - b[m]).max() < 1e-15
+
+
+@pytest.mark.parametrize("n", [8, 12, 16])
+def test_phase_free_forward_factorisation(n):
+    """The phase-free form of the tensor-core forward, replayed from the
+    library's host tables: with W_g kO = kappa_g + n m_g the row phase is
+    w_{8n}^{kappa_g . v} w_8^{m_g . v}; row g of each class core times
+    w_8^{m_g . v}, the sums scattered without phase, then the separable
+    modulation w_{8n}^{kappa_1} w_{8n}^{3 kappa_3} / 24 and the + sign DFT give
+    D x of the oracle."""
+    d = binding.describe(n)
+    W = binding.weyl_group().reshape(24, 3, 3).astype(np.int64)
+    v = np.array([1, 0, 3])
+    M = 8 * n
+    x = np.random.default_rng(n).standard_normal((n, n, n))
+    Zf = np.zeros((n, n, n), complex)
+    for o, k in enumerate(d["reps"]):
+        c = d["cls"][o]
+        wrap, canon = d["wrap"][c], d["canon"][c]
+        kap = W @ k - n * wrap
+        cg = np.exp(2j * np.pi * ((wrap @ v) % 8) / 8)
+        vals = cg * ((24 * d["fwd"][c]) @ x[kap[:, 0], kap[:, 1], kap[:, 2]])
+        for g in range(24):
+            if canon[g] == g:
+                Zf[tuple(kap[g])] = vals[g]
+    idx = np.arange(n)
+    Z = Zf * np.exp(2j * np.pi * idx / M)[:, None, None] * np.exp(2j * np.pi * 3 * idx / M)[None, None, :] / 24
+    y = np.fft.ifftn(Z) * n ** 3
+    ref = oracle.forward_sum_fft(x, n).reshape(n, n, n)
+    assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
