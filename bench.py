@@ -156,9 +156,17 @@ def cpu_baseline(n, seconds=12.0):
     t0 = time.perf_counter()
     oracle.forward_rows(x, n, rows, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the oracle's exchanged-sum form (orbit sums, then numpy's FFT) on one
+    # whole volume: the CPU counterpart of the F S factorisation, FP64
+    t0 = time.perf_counter()
+    oracle.forward_sum_fft(x, n)
+    dtf = time.perf_counter() - t0
     return {"value": len(rows) / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d output points (whole rows of D, 24 n^3 terms each) of one n=%d phantom volume, "
-                      "FP64 direct definition in C/OpenMP, %.1f s" % (len(rows), n, dt)}
+                      "FP64 direct definition in C/OpenMP, %.1f s" % (len(rows), n, dt),
+            "fft_form": {"value": n ** 3 / dtf / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one whole n=%d phantom volume, FP64 orbit sums + numpy FFT (one thread), "
+                                   "%.1f s" % (n, dtf)}}
 
 
 def run_reference(args):
