@@ -34,8 +34,9 @@ Column (efg, abc) of B_n^{-1} holds the b_n coordinates of that element:
 With B_n so defined, the factorisation is checked against the dense matrix
 of Def. 2 (tests/test_oracle_radix2.py) and ``forward_radix2`` evaluates it
 recursively down to D_2, the 2 x 2 x 2 transform from the definition.
-``python -m oracle.radix2`` prints the non-zeros of B_n and the error of the
-recursion evaluated in FP32 against the FP64 dense matrix.
+``python -m oracle.radix2`` prints the non-zeros of B_n, the complex
+multiply-adds per point of the whole recursion and its error evaluated in
+FP64 and in FP32 against the FP64 dense matrix.
 """
 import functools
 
@@ -200,16 +201,29 @@ def nonzeros_per_row(A, rel=1e-12):
     return float((A > rel * A.max()).sum()) / A.shape[0]
 
 
+def recursion_macs(n, skew=CANONICAL_SKEW, rel=1e-12):
+    """Complex multiply-adds of one transform by the recursion: the
+    non-zeros of B_n, 8 x 8 per column block of D_2 (x) 1, and the eight
+    sub-transforms (their shifts differ); D_2 itself dense (64)."""
+    if n == 2:
+        return 64
+    m = n // 2
+    B = np.abs(basis_change(n, skew))
+    own = int((B > rel * B.max()).sum()) + 64 * m ** 3
+    return own + sum(recursion_macs(m, sub_shift(skew, i), rel) for i in _BITS)
+
+
 def main():
     rng = np.random.default_rng(0)
-    print("n   nnz/row B_n   max|B_n|   rel L2 of the recursion vs the dense matrix: FP64   FP32   (F.S form in FP32: see bench)")
+    print("n   nnz/row B_n   max|B_n|   MACs/pt   rel L2 of the recursion vs the dense matrix: FP64   FP32")
     for n in (4, 8, 16):
         B = basis_change(n)
         x = rng.standard_normal(n ** 3)
         ref = dct_matrix(n) @ x
         e64 = np.linalg.norm(forward_radix2(x, n) - ref) / np.linalg.norm(ref)
         e32 = np.linalg.norm(forward_radix2(x.astype(np.float32), n, dtype=np.complex64) - ref) / np.linalg.norm(ref)
-        print("%-3d %-13.2f %-10.3g %-52.2e %.2e" % (n, nonzeros_per_row(B), np.abs(B).max(), e64, e32))
+        print("%-3d %-13.2f %-10.3g %-9.1f %-52.2e %.2e" % (n, nonzeros_per_row(B), np.abs(B).max(),
+                                                           recursion_macs(n) / n ** 3, e64, e32))
 
 
 if __name__ == "__main__":
