@@ -343,3 +343,50 @@ def test_tensor_core_inverse_and_adjoint(dtype, n, batch):
         assert rel(xi, xref) < TC_TOL, rel(xi, xref)
     assert rel(xi, xi32) < 2e-6, rel(xi, xi32)
     assert rel(xi, x) < 4e-5
+
+
+def test_tensor_core_forward_bench_configuration():
+    """The headline configuration as bench.py times it: order 128, batch 64,
+    BF16 terms, 8 MB chunks over 3 internal streams (the autotuner's pick on
+    GB300), row phase in the DFT passes; sampled rows of three volumes
+    against the oracle, and agreement with the plain FP32 form everywhere."""
+    n, batch = 128, 64
+    checked = [0, 31, 63]
+    x, hv = _full_size(n, batch, checked, seed=41, maker=inputs.phantom)
+    rng = np.random.default_rng(41)
+    with binding.Plan(n, batch, "r32_bf16x3") as p, binding.Plan(n, batch, "r32") as q:
+        p.set_schedule(chunk_mb=8, streams=3)
+        assert p.schedule()["tc_fold"] == 1
+        y = p.forward(x)
+        y32 = q.forward(x)
+        p.check()
+        for v in checked:
+            rows = rng.integers(0, n ** 3, size=24)
+            ref = oracle.forward_rows(hv[v].astype(np.float32).astype(np.float64), n, rows)
+            got = y[v * n ** 3 + torch.from_numpy(rows).to(DEV)].cpu().numpy()
+            rms = torch.sqrt(torch.mean(torch.abs(y[v * n ** 3:(v + 1) * n ** 3]) ** 2)).item()
+            est = np.sqrt(np.mean(np.abs(got - ref) ** 2)) / rms
+            assert est < TC_TOL, (v, est)
+        d = (torch.linalg.vector_norm(y - y32) / torch.linalg.vector_norm(y32)).item()
+        assert d < TC_TOL, d
+
+
+def test_maximum_order_sampled_rows_and_round_trip():
+    """The largest order a plan accepts (512: generic mixed-radix passes, 5.7 M
+    orbits), a pair of real volumes: sampled rows of the first against the
+    oracle and the round trip of both."""
+    n, batch = 512, 2
+    x, hv = _full_size(n, batch, [0], seed=5, maker=inputs.uniform)
+    rng = np.random.default_rng(512)
+    with binding.Plan(n, batch, "r32") as p:
+        y = p.forward(x)
+        back = p.inverse(y)
+        torch.cuda.synchronize()
+        err_rt = (torch.linalg.vector_norm(back - x) / torch.linalg.vector_norm(x)).item()
+        rows = rng.integers(0, n ** 3, size=8)
+        ref = oracle.forward_rows(hv[0].astype(np.float32).astype(np.float64), n, rows)
+        got = y[torch.from_numpy(rows).to(DEV)].cpu().numpy()
+        rms = torch.sqrt(torch.mean(torch.abs(y[:n ** 3]) ** 2)).item()
+    assert err_rt < 1e-5, err_rt
+    est = np.sqrt(np.mean(np.abs(got - ref) ** 2)) / rms
+    assert est < 1e-5, est
