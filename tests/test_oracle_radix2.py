@@ -69,3 +69,32 @@ def test_dropped_ideal_constant_is_caught(monkeypatch):
     monkeypatch.setattr(radix2, "ideal_values", lambda s: [0j, 0j, 0j])
     Binv = radix2.basis_change_inverse.__wrapped__(4, skew)
     assert np.abs(oracle.dct_matrix(4, skew) @ Binv - radix2.factor_product(4, skew)).max() > 1e-3
+
+
+def test_wrong_point_permutation_is_caught(monkeypatch):
+    """A planted mistake: P_n sending row (i, k) to 2i + k instead of i + 2k."""
+    n = 4
+    good = radix2.point_permutation
+
+    def swapped(m2):
+        m = m2 // 2
+        perm = good(m2).copy()
+        for row in range(m2 ** 3):
+            i, k = divmod(row, m ** 3)
+            i0, i1, i2 = (i >> 2) & 1, (i >> 1) & 1, i & 1
+            k0, k1, k2 = k // (m * m), (k // m) % m, k % m
+            perm[row] = ((2 * i0 + k0) * m2 + (2 * i1 + k1)) * m2 + (2 * i2 + k2)
+        return perm
+
+    monkeypatch.setattr(radix2, "point_permutation", swapped)
+    lhs = oracle.dct_matrix(n) @ radix2.basis_change_inverse(n)
+    assert np.abs(lhs - radix2.factor_product(n)).max() > 1e-3
+
+
+def test_sub_shift_without_halving_is_caught(monkeypatch):
+    """A planted mistake: the sub-transforms at c + i instead of (c + i)/2."""
+    n = 4
+    monkeypatch.setattr(radix2, "sub_shift", lambda skew, i: (tuple(int(skew[0][a]) + int(i[a]) * skew[1]
+                                                                    for a in range(3)), skew[1]))
+    lhs = oracle.dct_matrix(n) @ radix2.basis_change_inverse(n)
+    assert np.abs(lhs - radix2.factor_product(n)).max() > 1e-3
