@@ -178,3 +178,30 @@ def test_phase_free_forward_factorisation(n):
     y = np.fft.ifftn(Z) * n ** 3
     ref = oracle.forward_sum_fft(x, n).reshape(n, n, n)
     assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [8, 16, 24, 40, 64, 88, 96, 128])
+def test_pencil_pair_enumeration_writes_the_packed_layout(n):
+    """Replay of the fused split pass's pencil enumeration: primary pencils
+    (l, q) for l = 0 .. n/2 (row n/2: q < n/2) store Re y at their points,
+    their partners (n - l, q - l) (none for l = 0) store -Im y.  Every point of
+    the volume is written exactly once, Re exactly at the oracle's primary
+    points, and the partner pencil holds pi of the primary pencil's points."""
+    wrote = np.zeros((n, n, n), dtype=np.int8)     # +1 Re, -1 -Im
+    count = np.zeros((n, n, n), dtype=np.int32)
+    pi = oracle.conjugate_partner(n).reshape(n, n, n)
+    k = np.arange(n)
+    for l in range(n // 2 + 1):
+        qlim = n // 2 if 2 * l == n else n
+        for q in range(qlim):
+            wrote[k, l, q] = 1
+            count[k, l, q] += 1
+            if l == 0:
+                continue
+            lp, qp = (n - l) % n, (q - l) % n
+            wrote[k, lp, qp] = -1
+            count[k, lp, qp] += 1
+            # the counterpart of primary index k sits at k - l on the partner pencil
+            assert (pi[k, l, q] == ((k - l) % n) * n * n + lp * n + qp).all()
+    assert (count == 1).all()
+    assert ((wrote.reshape(-1) == 1) == oracle.packed_primary(n)).all()
