@@ -76,3 +76,28 @@ def test_wrong_packed_rule_is_caught(monkeypatch):
                        for a in range(n ** 3)])
     monkeypatch.setattr(oracle, "conjugate_partner", lambda m: bad_pi)
     assert np.abs(oracle.unpack_hermitian(oracle.pack_hermitian(y, n), n)[0] - y).max() > 1e-3
+
+
+def test_dropped_wrap_in_the_exchanged_sum_is_caught(monkeypatch):
+    """The exchanged-sum form with the phase taken at the reduced member
+    (w k mod n) instead of w k itself drops the 8th-root wrap factor of the
+    power form at theta = (c + idx)/n; the row pin at a large order catches it."""
+    n = 16
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((1, n, n, n))
+    rows = rng.integers(0, n ** 3, size=16)
+    ref = oracle.forward_rows(x[0], n, rows)
+    assert np.abs(oracle.forward_sum_fft(x, n).reshape(-1)[rows] - ref).max() < 1e-10
+
+    def bad_maps(m, skew):
+        a, d = skew
+        k = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"), -1).reshape(-1, 3)
+        out = []
+        for w in oracle.weyl_group():
+            kap = np.mod(k @ w.T, m)
+            flat = (kap[:, 0] * m + kap[:, 1]) * m + kap[:, 2]
+            out.append((flat, np.exp(2j * np.pi * np.mod(kap @ np.asarray(a), d * m) / (d * m))))
+        return out
+
+    monkeypatch.setattr(oracle, "_orbit_maps", bad_maps)
+    assert np.abs(oracle.forward_sum_fft(x, n).reshape(-1)[rows] - ref).max() > 1e-3 * np.abs(ref).max()

@@ -248,14 +248,62 @@ def test_shift_property(n):
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8])
 def test_sum_fft_form_matches_dense(n):
     x = RNG.standard_normal((2, n, n, n)) + 1j * RNG.standard_normal((2, n, n, n))
-    if n ** 3 <= 512:
-        ref = oracle.forward_dense(x, n)
-        assert np.abs(oracle.forward_sum_fft(x, n) - ref).max() < 1e-12 * max(1, n ** 1.5)
-        assert np.abs(oracle.adjoint_sum_fft(x, n) - oracle.adjoint_dense(x, n)).max() < 1e-12 * max(1, n ** 1.5)
-    else:
-        rows = RNG.integers(0, n ** 3, size=40)
-        ref = oracle.forward_rows(x[0], n, rows)
-        assert np.abs(oracle.forward_sum_fft(x, n)[0].reshape(-1)[rows] - ref).max() < 1e-11
+    ref = oracle.forward_dense(x, n)
+    assert np.abs(oracle.forward_sum_fft(x, n) - ref).max() < 1e-12 * max(1, n ** 1.5)
+    assert np.abs(oracle.adjoint_sum_fft(x, n) - oracle.adjoint_dense(x, n)).max() < 1e-12 * max(1, n ** 1.5)
+
+
+def _orbit_size_mod_n(k, n):
+    W = oracle.weyl_group()
+    return len({tuple(int(c) for c in np.mod(w @ np.asarray(k), n)) for w in W})
+
+
+def _special_indices(n, rng, want):
+    """Flat indices of the grid that sit on the walls of the fundamental
+    alcove {k >= 0, k1 + k2 + k3 <= n} modulo n, i.e. whose W-orbit in
+    Z_n^3 has fewer than 24 members (the boundary classes of the orbit
+    partition), plus the corners of the box."""
+    out = [0, n ** 3 - 1]
+    tries = 0
+    while len(out) < want and tries < 20000:
+        tries += 1
+        k = rng.integers(0, n, size=3)
+        c = rng.integers(0, 5)
+        if c == 0:
+            k[rng.integers(0, 3)] = 0
+        elif c == 1:
+            k[2] = (n - k[0] - k[1]) % n
+        elif c == 2:
+            k[1] = k[0]
+        elif c == 3:
+            k[:] = [k[0], 0, k[0]]
+        else:
+            k[:] = [(n // 2) * rng.integers(0, 2), (n // 2) * rng.integers(0, 2), (n // 2) * rng.integers(0, 2)]
+        if _orbit_size_mod_n(k, n) < 24:
+            out.append(int((k[0] * n + k[1]) * n + k[2]))
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("n", [16, 24, 40, 64, 96, 128])
+def test_sum_fft_form_matches_definition_rows_at_large_orders(n):
+    """The exchanged-sum + FFT form (the full-volume comparator of the GPU
+    tests) against the plain definition of Def. 2 evaluated row by row in C
+    with exact integer phases: 48 uniform rows and 16 rows/columns on the
+    alcove walls (non-free orbits, where the wrap of w k modulo n and the
+    coinciding slots matter), forward and adjoint, complex input."""
+    rng = np.random.default_rng(1000 + n)
+    x = rng.standard_normal((1, n, n, n)) + 1j * rng.standard_normal((1, n, n, n))
+    idx = np.concatenate([rng.integers(0, n ** 3, size=48), _special_indices(n, rng, 16)])
+    sizes = [_orbit_size_mod_n(np.unravel_index(i, (n, n, n)), n) for i in idx[48:]]
+    assert min(sizes) < 24 and len(idx) == 64
+    y = oracle.forward_sum_fft(x, n).reshape(-1)
+    ref = oracle.forward_rows(x[0], n, idx)
+    scale = np.sqrt(np.mean(np.abs(y) ** 2))
+    assert np.abs(y[idx] - ref).max() < 1e-13 * n * scale, np.abs(y[idx] - ref).max() / scale
+    a = oracle.adjoint_sum_fft(x, n).reshape(-1)
+    aref = oracle.adjoint_rows(x[0], n, idx)
+    scale = np.sqrt(np.mean(np.abs(a) ** 2))
+    assert np.abs(a[idx] - aref).max() < 1e-13 * n * scale, np.abs(a[idx] - aref).max() / scale
 
 
 @pytest.mark.parametrize("n", [3, 5])
