@@ -443,6 +443,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
     ap.add_argument("--autotune", type=int, default=1, help="run fcc_dct_autotune before timing (1) or not (0)")
+    ap.add_argument("--sched", default="",
+                    help="schedule keys applied after the autotuner, e.g. 'tc_ws=0,streams=1'")
     ap.add_argument("--output", default="complex", choices=["complex", "packed"],
                     help="forward output: complex64 point values, or the Hermitian-packed reals of real plans")
     args = ap.parse_args()
@@ -483,6 +485,9 @@ def main():
 
     # the library's autotuner picks the execution schedule once (untimed)
     sched = plan.autotune(x, y, reps=3)[1] if args.autotune else plan.schedule()
+    if args.sched:
+        plan.set_schedule(**{k: int(v) for k, v in (kv.split("=") for kv in args.sched.split(","))})
+        sched = plan.schedule()
     for _ in range(args.warmup):
         fwd()
     torch.cuda.synchronize()

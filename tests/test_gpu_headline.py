@@ -7,9 +7,11 @@ by element with the oracle's FP64 exchanged-sum form of Def. 2 (itself
 pinned against the row-by-row definition at this order in
 tests/test_oracle_pins.py).  Bars: relative L2 over the volume 1e-6 for the
 tensor-core dtypes and 1e-5 for the plain FP32 form; per element the error
-stays within a fraction of the volume's RMS (FFT rounding is absolute at
-the scale of the whole output) plus 1e-6 of the entry itself (the large
-low-frequency entries).
+is bounded by a fraction of the RMS of the volume plus the RMS of the
+output's own pencil along the slow axis (the last DFT pass sums that
+pencil, so its FP32 rounding is absolute at the pencil's scale: CT-like
+phantoms put a large share of the energy into the pencils through the
+low frequencies), plus 1e-6 of the entry itself.
 """
 import numpy as np
 import pytest
@@ -49,12 +51,19 @@ def headline():
 
 
 def _check_volume(got, ref, rel_bar, elem_bar, what):
+    got = got.reshape(N, N, N)
+    ref = ref.reshape(N, N, N)
     err = np.abs(got - ref)
     rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    pencil = np.sqrt(np.mean(np.abs(ref) ** 2, axis=0, keepdims=True))   # slow-axis pencils
     r = _rel(got, ref)
     assert r < rel_bar, (what, "rel L2", r)
-    worst = float(np.max(err / (elem_bar * rms + 1e-6 * np.abs(ref))))
-    assert worst <= 1.0, (what, "per element", worst, float(err.max() / rms))
+    ratio = err / (elem_bar * (rms + pencil) + 1e-6 * np.abs(ref))
+    at = np.unravel_index(int(np.argmax(ratio)), ratio.shape)
+    worst = float(ratio[at])
+    assert worst <= 1.0, (what, "per element", worst, "rel L2", r, "max err / rms", float(err.max() / rms),
+                          "at", tuple(int(v) for v in at), "|ref| / rms", float(np.abs(ref[at]) / rms),
+                          "pencil rms / rms", float(pencil[(0,) + at[1:]] / rms))
     return r
 
 
