@@ -37,6 +37,30 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def l2_copy_peak(device):
+    """Copy rate of an L2-resident buffer (read + write bytes per second, GB/s):
+    torch's copy kernel over two buffers of 16-32 MB each (together below the
+    126 MB L2), timed with CUDA events after a warm-up; the best size."""
+    import torch
+    best = 0.0
+    for mb in (16, 24, 32):
+        n = mb * 2 ** 20 // 4
+        a = torch.rand(n, device=device)
+        b = torch.empty_like(a)
+        for _ in range(20):
+            b.copy_(a)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * n * 4 * 200 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        del a, b
+    return best
+
+
 def slowest_rank_ms(ms, dist, device):
     """Replicas: every rank times its own batch; the job's time is the slowest
     rank's (no data-path collective, only this reduction)."""
@@ -370,6 +394,29 @@ def secondary_configs(dev):
     return out
 
 
+def host_link_rates(dev, nbytes):
+    """Pinned host <-> device copy rates (GB/s) for a buffer of nbytes, CUDA
+    events around 3 copies each way after one warm-up copy: the link that
+    bounds the end-to-end numbers."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d_gbs", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_gbs", lambda: h.copy_(d, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del h, d
+    return out
+
+
 def packed_vs_complex(pk, y, n, batch, dev):
     """Relative L2 between the packed output and the complex output of the
     same plan re-laid out (primary points keep Re y, the others -Im y)."""
@@ -412,13 +459,17 @@ def packed_config(plan, x, y, n, batch, args, dev, st):
     plan.forward_packed_host(xh, pkh)
     torch.cuda.synchronize()
     ke = max(3, args.steps // 4)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(ke):
-        plan.forward_packed_host(xh, pkh)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / ke
+    runs = []
+    for _ in range(3):   # three timings in the same run: the spread shows how steady the link is
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(ke):
+            plan.forward_packed_host(xh, pkh)
+        e1.record(st)
+        torch.cuda.synchronize()
+        runs.append(e0.elapsed_time(e1) / ke)
+    ms_e2e = statistics.median(runs)
+    link = host_link_rates(dev, pts * 4)
     peak, kind = _peaks()
     return {"value": pts / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "form": args.dtype,
             "output": "Hermitian-packed reals (n^3 per volume)", "bytes_per_point": 8,
@@ -426,7 +477,9 @@ def packed_config(plan, x, y, n, batch, args, dev, st):
             "launches": plan.launches(3), "kernels_ms": kern, "rel_diff_vs_complex_output": diff,
             "roundtrip_rel_l2": rt,
             "e2e": {"value": pts / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": pts * 4,
-                    "d2h_bytes_per_step": pts * 4}}
+                    "d2h_bytes_per_step": pts * 4, "ms_per_step_runs": runs,
+                    "pinned_copy_gbs": link,
+                    "link_bound_ms": pts * 4 / (min(link["h2d_gbs"], link["d2h_gbs"]) * 1e9) * 1e3}}
 
 
 def main():
@@ -535,7 +588,13 @@ def main():
     per_launch_ms = top_ms / top_cnt
     per_launch_pts = pts * args.steps / top_cnt
     peak, peak_kind = _peaks()
-    achieved = algo_bytes.get(top_name, 12) * per_launch_pts / (per_launch_ms * 1e-3) / 1e9
+    l2_peak = l2_copy_peak(dev)
+    # the roofline unit is the whole forward's algorithmic bytes per point
+    # (12: FP32 in, complex64 out; 8 with the packed output), charged to the
+    # dominant kernel per point it processes; the kernel's own paired bytes
+    # (what it reads and writes itself) are reported beside it
+    achieved = step_bytes * per_launch_pts / (per_launch_ms * 1e-3) / 1e9
+    own_gbs = algo_bytes.get(top_name, 12) * per_launch_pts / (per_launch_ms * 1e-3) / 1e9
     traffic = _traffic(top_name, per_launch_pts) if n == 128 else None
     step_gbs = step_bytes * pts / (ms * 1e-3) / 1e9
 
@@ -564,6 +623,7 @@ def main():
     e3.record(st)
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3) / ke
+    link = host_link_rates(dev, pts * 4)
 
     # the comparison form on the same inputs (same timing rules)
     compare = None
@@ -627,17 +687,22 @@ def main():
                              % (pts * 4 / 1e6, pts * (step_bytes - 4) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_point": algo_bytes.get(top_name, 12)},
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_point": step_bytes,
+                         "kernel_own_bytes_per_point": algo_bytes.get(top_name, 12),
+                         "kernel_own_achieved": own_gbs, "kernel_own_frac": own_gbs / peak,
+                         "l2": {"peak": l2_peak, "unit": "GB/s", "frac": own_gbs / l2_peak,
+                                "kind": "measured copy of an L2-resident buffer (read + write)"}},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": step_bytes},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "kernels": {k: {"launches_per_step": v[1] / args.steps, "ms_per_launch": v[0] / v[1],
                             "achieved_gbs": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9,
-                            "frac": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9 / peak}
+                            "frac": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9 / peak,
+                            "frac_l2": algo_bytes.get(k, 12) * pts / (v[0] / args.steps * 1e-3) / 1e9 / l2_peak}
                         for k, v in kern.items()},
             "kernel_timing": "CUDA events around each launch, one internal stream (each kernel alone)",
             "e2e": {"value": world * pts / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
-                    "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * yh.element_size())},
+                    "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
+                    "pinned_copy_gbs": link},
             "gpu_launches": plan.launches(3 if packed else 0) * args.steps,
             "clocks": ck,
             "accuracy": accuracy,

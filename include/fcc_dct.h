@@ -219,7 +219,9 @@ int fcc_dct_profile_read(fcc_plan* plan, char* names, double* ms, int* launches,
  * the last call's contents; nothing in it needs to start at zero (every
  * value is written before it is read).  Calls whose work overlaps on the GPU
  * (different streams, or different host threads) race on the array and
- * must be serialised by the caller.
+ * must be serialised by the caller.  Like the other entry points it returns
+ * FCC_ERR_TIMEOUT (and clears the plan's status word) when an earlier call
+ * of the plan recorded a device-side timeout.
  */
 #define FCC_STATIC_SCRATCH_BYTES (16u << 20)
 fcc_status fcc_dct_inverse_static(fcc_plan* plan, const void* in, void* out, void* stream);
@@ -247,6 +249,23 @@ fcc_status fcc_dct_check(fcc_plan* plan);
  * FCC_ERR_UNSUPPORTED for plans without a tensor-core form.
  */
 fcc_status fcc_dct_test_wait_timeout(fcc_plan* plan, int enable);
+
+/*
+ * Test hooks for host-side allocation failure (no counterpart in the paper;
+ * nothing on the GPU is made to fail).  fcc_dct_test_fail_alloc(nth) arms a
+ * one-shot failure: counting from the call, the nth allocation the library
+ * makes in this process -- the plan object (host), the pinned status word, a
+ * device table or workspace (plan creation, the first packed or host-buffer
+ * call) -- reports failure instead, as an exhausted allocator would.  The
+ * entry point that made it returns NULL (plans) or FCC_ERR_ALLOC after
+ * releasing what it had allocated.  nth = 0 disarms; nth < 0 is
+ * FCC_ERR_INVALID_ARG.  fcc_dct_test_allocations reports what the library
+ * holds right now: the number of live plans and the device bytes they own
+ * (through *plans and *device_bytes when not NULL); returns the number of
+ * allocations made since the process started.
+ */
+fcc_status fcc_dct_test_fail_alloc(int nth);
+int64_t fcc_dct_test_allocations(int64_t* plans, int64_t* device_bytes);
 
 /*
  * Execution schedule.  The paper has no counterpart: these knobs change only

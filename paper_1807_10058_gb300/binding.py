@@ -23,7 +23,8 @@ EXPORTS = [
     "fcc_dct_profile_enable", "fcc_dct_profile_read", "fcc_dct_inverse_static", "fcc_dct_check",
     "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune", "fcc_dct_test_wait_timeout",
     "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
-    "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host",
+    "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host", "fcc_dct_test_fail_alloc",
+    "fcc_dct_test_allocations",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -92,6 +93,10 @@ def lib():
         L.fcc_dct_autotune.restype = i32
         L.fcc_dct_test_wait_timeout.argtypes = [vp, i32]
         L.fcc_dct_test_wait_timeout.restype = i32
+        L.fcc_dct_test_fail_alloc.argtypes = [i32]
+        L.fcc_dct_test_fail_alloc.restype = i32
+        L.fcc_dct_test_allocations.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.fcc_dct_test_allocations.restype = i64
         _LIB = L
     return _LIB
 
@@ -133,6 +138,13 @@ def describe(order, skew=None):
     return {"reps": k, "cls": cls, "free_class": fc.value, "wrap": wrap.reshape(-1, 24, 3),
             "canon": canon.reshape(-1, 24), "fwd": cx[0], "inv": cx[1], "adj": cx[2],
             "invertible": bool(inv_ok.value)}
+
+
+def allocations():
+    """(allocations made so far, live plans, device bytes the live plans own)."""
+    plans, dev = ctypes.c_int64(), ctypes.c_int64()
+    seq = lib().fcc_dct_test_allocations(ctypes.byref(plans), ctypes.byref(dev))
+    return seq, plans.value, dev.value
 
 
 def weyl_group():

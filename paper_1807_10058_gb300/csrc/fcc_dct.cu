@@ -125,6 +125,7 @@ struct fcc_plan {
     cudaStream_t copy_in = nullptr, copy_out = nullptr;   // *_host: copies overlapping the transform
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_host = nullptr;
     std::vector<void*> allocs;
+    std::vector<int64_t> alloc_bytes;   // sizes of allocs (live-byte bookkeeping)
     // chunked schedule: volumes per chunk and internal streams (fork / join
     // with the caller's stream through events)
     int64_t chunk_bytes = 32ll << 20;
@@ -168,15 +169,30 @@ std::vector<T> to_pairs(const std::vector<cd>& v) {
     return out;
 }
 
+// Allocation bookkeeping and the one-shot failure of fcc_dct_test_fail_alloc.
+std::atomic<int64_t> g_alloc_seq{0};       // allocations made so far
+std::atomic<int64_t> g_fail_at{0};         // sequence number that fails (0: none)
+std::atomic<int64_t> g_live_plans{0};
+std::atomic<int64_t> g_live_dev_bytes{0};
+
+// true if this allocation is the armed one (the hook disarms itself)
+bool injected_failure() {
+    const int64_t seq = ++g_alloc_seq;
+    int64_t want = g_fail_at.load();
+    return want != 0 && seq == want && g_fail_at.compare_exchange_strong(want, 0);
+}
+
 fcc_status dev_alloc(fcc_plan* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return FCC_OK;
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    if (injected_failure() || cudaMalloc(ptr, bytes) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
         return FCC_ERR_ALLOC;
     }
     p->allocs.push_back(*ptr);
+    p->alloc_bytes.push_back((int64_t)bytes);
+    g_live_dev_bytes += (int64_t)bytes;
     return FCC_OK;
 }
 
@@ -373,6 +389,8 @@ void release(fcc_plan* p) {
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
     for (void* a : p->allocs) cudaFree(a);
+    for (int64_t b : p->alloc_bytes) g_live_dev_bytes -= b;
+    --g_live_plans;
     for (auto& r : p->recs) { if (r.a) cudaEventDestroy(r.a); if (r.b) cudaEventDestroy(r.b); }
     for (int i = 0; i < kMaxStreams; ++i) {
         if (p->streams[i]) cudaStreamDestroy(p->streams[i]);
@@ -405,9 +423,10 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype, const int* v = nu
     if (orders.empty()) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     for (int n : orders)
         if (n < 1 || n > FCC_MAX_ORDER) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
-    fcc_plan* p = new (std::nothrow) fcc_plan();
+    fcc_plan* p = injected_failure() ? nullptr : new (std::nothrow) fcc_plan();
     if (!p) { fail(FCC_ERR_ALLOC); return nullptr; }
-    if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); delete p; fail(FCC_ERR_CUDA); return nullptr; }
+    ++g_live_plans;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); --g_live_plans; delete p; fail(FCC_ERR_CUDA); return nullptr; }
     p->dtype = dtype;
     if (v && !canonical_shift(v, d)) {   // (1/8, 0, 3/8) in other terms keeps the canonical tables
         for (int i = 0; i < 3; ++i) p->shift_v[i] = v[i];
@@ -430,7 +449,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype, const int* v = nu
     if (p->num_sms < 1) p->num_sms = 1;
     fcc_status s = upload_group();
     if (s == FCC_OK) {
-        if (cudaHostAlloc((void**)&p->h_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+        if (injected_failure() || cudaHostAlloc((void**)&p->h_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
             cudaGetLastError();
             p->h_status = nullptr;
             s = FCC_ERR_ALLOC;
@@ -1841,6 +1860,18 @@ fcc_status fcc_dct_check(fcc_plan* p) {
     return s == FCC_OK ? FCC_OK : fail(s);
 }
 
+fcc_status fcc_dct_test_fail_alloc(int nth) {
+    if (nth < 0) return fail(FCC_ERR_INVALID_ARG);
+    g_fail_at = nth == 0 ? 0 : g_alloc_seq.load() + nth;
+    return FCC_OK;
+}
+
+int64_t fcc_dct_test_allocations(int64_t* plans, int64_t* device_bytes) {
+    if (plans) *plans = g_live_plans.load();
+    if (device_bytes) *device_bytes = g_live_dev_bytes.load();
+    return g_alloc_seq.load();
+}
+
 fcc_status fcc_dct_last_error(void) { return g_last; }
 
 const char* fcc_status_string(fcc_status s) {
@@ -1966,8 +1997,8 @@ fcc_status run_inverse_static(fcc_plan* p, const float* in, float* out, float2* 
         }
         const int64_t npairs = (rin && nvol >= 2) ? nvol / 2 : 0;
         for (int64_t q = 0; q < npairs && !s; ++q) {
-            s = launch_pair(false, t.n, y + q * 4 * n3, (float*)ws, 1, st);
-            if (!s) s = launch_dft3(t, -1, (const float*)ws, (float*)ws, 1, st);
+            // pair merge fused into the first DFT pass where the buffers allow
+            s = merge_dft3_pairs(t, y + q * 4 * n3, (float*)ws, 1, st);
             if (!s) s = launch_mix_tiled(t, MODE_INV, false, true, (const float*)ws, x + q * 2 * n3, 1, scale, st, true);
         }
         for (int64_t u = 2 * npairs; u < nvol && !s; ++u) {
@@ -1984,6 +2015,12 @@ fcc_status run_inverse_static(fcc_plan* p, const float* in, float* out, float2* 
 
 extern "C" fcc_status fcc_dct_inverse_static(fcc_plan* p, const void* in, void* out, void* stream) {
     if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    // a device-side timeout recorded by an earlier call of the plan surfaces
+    // here, as in every other entry point
+    if (*(volatile int*)p->h_status != 0) {
+        *(volatile int*)p->h_status = 0;
+        return fail(FCC_ERR_TIMEOUT);
+    }
     if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, 1);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, 1);

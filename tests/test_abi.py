@@ -90,3 +90,25 @@ def test_schedule_calls_reject_null_plan():
 
 def test_wait_timeout_hook_rejects_null_plan():
     assert binding.lib().fcc_dct_test_wait_timeout(None, 1) == binding.FCC_ERR_INVALID_ARG
+
+
+def test_injected_allocation_failure_of_the_plan_object():
+    """The first allocation of plan creation (the host plan object) fails on
+    request: NULL, FCC_ERR_ALLOC, no plan left alive, the hook disarmed.
+    Runs without a GPU: nothing before that allocation touches the device."""
+    L = binding.lib()
+    assert L.fcc_dct_test_fail_alloc(-1) == binding.FCC_ERR_INVALID_ARG
+    seq0, plans0, dev0 = binding.allocations()
+    assert L.fcc_dct_test_fail_alloc(1) == binding.FCC_OK
+    assert not L.fcc_dct_plan(8, 2, 2)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_ALLOC
+    seq1, plans1, dev1 = binding.allocations()
+    assert seq1 == seq0 + 1 and plans1 == plans0 and dev1 == dev0
+    # disarmed: the next failure (if any) is not an allocation failure
+    assert L.fcc_dct_test_fail_alloc(0) == binding.FCC_OK
+    h = L.fcc_dct_plan(8, 2, 2)
+    if h:
+        L.fcc_dct_destroy(h)
+    else:
+        assert L.fcc_dct_last_error() != binding.FCC_ERR_ALLOC
+    assert binding.allocations()[1] == plans0

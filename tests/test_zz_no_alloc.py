@@ -53,6 +53,38 @@ def test_static_inverse_matches_inverse_twice(order, batch, dtype):
             assert _rel(got, x) < 4 * TOL
 
 
+@pytest.mark.parametrize("orders,dtype", [([8, 8, 8, 16, 24, 24, 24], "r32"), ([5, 8, 8, 8, 16, 24, 24, 24], "r32"),
+                                          ([24, 64, 16], "c32")])
+def test_static_inverse_ragged_plans_match_inverse(orders, dtype):
+    """Ragged plans: mixed orders in one plan, odd counts per order (the
+    single leftover volume of a real plan), and volume bases that are only
+    8-byte aligned after an odd order (the generic DFT and pair-merge paths)."""
+    vols = [inputs.smoothed_noise(n, 1, seed=40 + i)[0] for i, n in enumerate(orders)]
+    flat = np.concatenate([v.reshape(-1) for v in vols])
+    if dtype == "c32":
+        flat = flat + 1j * np.roll(flat, 5)
+    with binding.Plan(orders=orders, dtype=dtype) as p:
+        x = torch.from_numpy(flat.astype(np.float32 if dtype == "r32" else np.complex64)).to(DEV)
+        y = p.forward(x)
+        ref = p.inverse(y)
+        for call in range(2):
+            got = _static_inverse(p, y)
+            torch.cuda.synchronize()
+            assert _rel(got, ref) < TOL, (call, _rel(got, ref))
+        assert _rel(got, x) < 4 * TOL
+
+
+def test_static_inverse_complex_plan_at_a_fast_order():
+    n, batch = 64, 3
+    with binding.Plan(n, batch, "c32") as p:
+        x = torch.from_numpy(inputs.uniform(n, batch, seed=9, complex_=True).astype(np.complex64).reshape(-1)).to(DEV)
+        y = p.forward(x)
+        ref = p.inverse(y)
+        got = _static_inverse(p, y)
+        torch.cuda.synchronize()
+        assert _rel(got, ref) < TOL and _rel(got, x) < 4 * TOL
+
+
 def test_static_inverse_rejects_what_does_not_fit():
     with binding.Plan(8, 1, "r64") as p:   # FP64 plans are not served
         y = torch.zeros(8 ** 3, dtype=torch.complex128, device=DEV)
