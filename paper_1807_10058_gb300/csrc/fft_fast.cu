@@ -2,6 +2,7 @@
 // kept in their own translation unit so they compile in parallel with the
 // rest of the library.
 #include "fft_fast.cuh"
+#include "fft_slab128.cuh"
 
 namespace fcc {
 
@@ -24,6 +25,17 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
     if (slab) {
         const int64_t g = nvol * N;
         if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+        if constexpr (N == 128) {   // 16 warps per slab, exchange inside the slab
+            static DeviceOnce attr128;
+            if (!attr128.done()) {
+                cudaFuncSetAttribute(fft_slab128_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlab128Smem);
+                cudaFuncSetAttribute(fft_slab128_kernel<-1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlab128Smem);
+                attr128.mark();
+            }
+            if (sign > 0) fft_slab128_kernel<1, false><<<(unsigned)g, kSlab128Threads, kSlab128Smem, st>>>(in, out, tw, vstride, voff, nullptr);
+            else fft_slab128_kernel<-1, false><<<(unsigned)g, kSlab128Threads, kSlab128Smem, st>>>(in, out, tw, vstride, voff, nullptr);
+            return cudaGetLastError();
+        }
         if (sign > 0) fft_slab_kernel<N, 1><<<(unsigned)g, L::SLAB_THREADS, L::slab_smem, st>>>(in, out, tw, vstride, voff);
         else fft_slab_kernel<N, -1><<<(unsigned)g, L::SLAB_THREADS, L::slab_smem, st>>>(in, out, tw, vstride, voff);
     } else {
@@ -73,6 +85,15 @@ cudaError_t launch_slab_pre_n(const float2* in, float2* out, int64_t nvol, const
     }
     const int64_t g = nvol * N;
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if constexpr (N == 128) {
+        static DeviceOnce attr128;
+        if (!attr128.done()) {
+            cudaFuncSetAttribute(fft_slab128_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlab128Smem);
+            attr128.mark();
+        }
+        fft_slab128_kernel<1, true><<<(unsigned)g, kSlab128Threads, kSlab128Smem, st>>>(in, out, tw, vstride, nullptr, pre);
+        return cudaGetLastError();
+    }
     fft_slab_kernel<N, 1, true><<<(unsigned)g, L::SLAB_THREADS, smp, st>>>(in, out, tw, vstride, nullptr, pre);
     return cudaGetLastError();
 }
