@@ -391,6 +391,32 @@ def secondary_configs(dev):
                             "kernels_ms": kern, "accuracy_probe": sampled_accuracy(x, y, n, dev, skew=skew),
                             "form": "r32: tiled orbit mixing on staged class cores + register-radix DFT passes"}
     del x, y
+    # the paper's radix-2x2x2 recursion (Sec. 4.B) at order 16: the GPU
+    # evaluation in FP64 and FP32 beside the F S form on the same complex
+    # inputs, its operation counts and how its FP32 form rounds
+    n, b = 16, 64
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(16)
+    xc = torch.randn(b * n ** 3, dtype=torch.complex128, device=dev, generator=gen)
+    r2 = {"order": n, "batch": b}
+    with binding.Plan(n, b, "c64") as q:
+        yf = q.forward(xc)
+        r2["fs_c64_ms"] = _time(lambda: q.forward(xc, out=yf), 10, 3)
+    with binding.Plan(n, b, "c64", radix2=True) as q:
+        y64 = q.forward(xc)
+        r2["radix2_c64_ms"] = _time(lambda: q.forward(xc, out=y64), 10, 3)
+        r2["launches"] = q.launches(0)
+        r2["macs_per_point"] = q.radix2_stats(0)
+        r2["nnz_per_row_B"] = {k: q.radix2_stats(k)[0] for k in (4, 8, 16)}
+        r2["max_abs_B"] = {k: q.radix2_stats(k)[1] for k in (4, 8, 16)}
+    with binding.Plan(n, b, "c32", radix2=True) as q:
+        x32 = xc.to(torch.complex64)
+        y32 = q.forward(x32)
+        r2["radix2_c32_ms"] = _time(lambda: q.forward(x32, out=y32), 10, 3)
+    r2["rel_diff_radix2_c64_vs_fs_c64"] = (torch.linalg.vector_norm(y64 - yf) / torch.linalg.vector_norm(yf)).item()
+    r2["rel_diff_radix2_c32_vs_radix2_c64"] = (torch.linalg.vector_norm(y32.to(torch.complex128) - y64)
+                                               / torch.linalg.vector_norm(y64)).item()
+    out["radix2_n16_b64"] = r2
     return out
 
 

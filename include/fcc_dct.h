@@ -86,6 +86,38 @@ typedef enum {
 fcc_plan* fcc_dct_plan(int order, int batch, int dtype);
 
 /*
+ * The paper's own fast algorithm (Sec. 4.B, eq. FastAlgorithm): the radix-2x2x2
+ * factorisation
+ *   DCT_n(c) = P_n . (sum over i in {0,1}^3 of DCT_m((c + i)/2)) . (DCT_2(c) (x) 1_{m^3}) . B_n(c),
+ * n = 2m, evaluated recursively on the GPU down to the 8 x 8 DCT_2 of Def. 2.
+ * The basis change B_n, which the paper leaves to future work, is derived from
+ * its definition at plan time: B_n^{-1} column (efg, abc) is T_{abc} T_{m(e,f,g)}
+ * expanded with the mother recurrence (Prop. 1 (iv)) and reduced with the
+ * ideal T_{n e_j} = T_{e_j}(c) (Lemma 2), assembled in FP64 on the host and
+ * inverted on the GPU.  A second, independent evaluation of the transform
+ * (not the fast path: its FP32 error grows about tenfold per level, and B_n is
+ * dense-stored).  order: 2, 4, 8 or 16; dtype: FCC_C64 (FP64) or FCC_C32 (FP32
+ * arithmetic throughout, to measure how the recursion rounds); v, d: the shift
+ * c = v / d (v = NULL: (1/8, 0, 3/8)).  The plan serves fcc_dct_forward only
+ * (complex coefficients in, complex point values out, the layouts of the
+ * other plans); every other call on it returns FCC_ERR_UNSUPPORTED.  Plan
+ * creation synchronises the device and takes up to a few seconds at order 16
+ * (B_16 is 4096 x 4096).  NULL on error: FCC_ERR_INVALID_ARG, FCC_ERR_ALLOC,
+ * FCC_ERR_UNSUPPORTED (a singular B_n^{-1}).
+ */
+fcc_plan* fcc_dct_plan_radix2(int order, int batch, int dtype, const int* v, int d);
+
+/*
+ * Statistics of a radix-2 plan: level = k (k = order, order/2, ... >= 4):
+ * non-zeros per row of B_k (entries above 1e-12 of the largest, averaged over
+ * the level's shifts) and its largest |entry|, returns the number of shifts at
+ * that level; level = 0: complex multiply-adds per point of one transform
+ * (the non-zeros of every B_k, 64 per column block of DCT_2 (x) 1, 64 per
+ * DCT_2), returns 0.  -1 (FCC_ERR_INVALID_ARG) for other plans or levels.
+ */
+int fcc_dct_radix2_stats(const fcc_plan* plan, int level, double* nnz_per_row, double* max_abs, double* macs_per_point);
+
+/*
  * Plan for a ragged batch: `count` volumes whose orders are orders[0..count)
  * stored back to back (volume v starts at sum_{u<v} orders[u]^3 values).
  * Same layouts and dtypes as fcc_dct_plan.  `orders` is a host array read

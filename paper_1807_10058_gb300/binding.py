@@ -24,7 +24,7 @@ EXPORTS = [
     "fcc_dct_set_schedule", "fcc_dct_get_schedule", "fcc_dct_autotune", "fcc_dct_test_wait_timeout",
     "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
     "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host", "fcc_dct_test_fail_alloc",
-    "fcc_dct_test_allocations",
+    "fcc_dct_test_allocations", "fcc_dct_plan_radix2", "fcc_dct_radix2_stats",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -53,6 +53,11 @@ def lib():
         L.fcc_dct_plan_ragged.restype = vp
         L.fcc_dct_plan_skew.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
         L.fcc_dct_plan_skew.restype = vp
+        L.fcc_dct_plan_radix2.argtypes = [i32, i32, i32, ctypes.POINTER(i32), i32]
+        L.fcc_dct_plan_radix2.restype = vp
+        L.fcc_dct_radix2_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]
+        L.fcc_dct_radix2_stats.restype = i32
         L.fcc_dct_describe_skew.argtypes = [i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                             ctypes.POINTER(i32), ctypes.POINTER(i32)] + [vp] * 7
         L.fcc_dct_describe_skew.restype = i32
@@ -162,11 +167,16 @@ class Plan:
     (r, s, t) = v / d (uniform batches).  Owns the library handle; release
     with close() or `with`."""
 
-    def __init__(self, order=None, batch=1, dtype="r32", orders=None, skew=None):
+    def __init__(self, order=None, batch=1, dtype="r32", orders=None, skew=None, radix2=False):
         import torch  # noqa: F401  (initialises the CUDA context torch uses)
         L = lib()
         self.dtype_code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-        if orders is not None:
+        if radix2:
+            v, d = skew if skew is not None else ((1, 0, 3), 8)
+            varr = (ctypes.c_int * 3)(*[int(a) for a in v])
+            h = L.fcc_dct_plan_radix2(int(order), int(batch), self.dtype_code, varr, int(d))
+            self.orders = [int(order)] * int(batch)
+        elif orders is not None:
             arr = (ctypes.c_int * len(orders))(*[int(o) for o in orders])
             h = L.fcc_dct_plan_ragged(arr, len(orders), self.dtype_code)
             self.orders = [int(o) for o in orders]
@@ -202,6 +212,16 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def radix2_stats(self, level):
+        """Radix-2 plans: (non-zeros per row of B_level, its largest |entry|,
+        shifts at that level), or the complex multiply-adds per point of one
+        transform for level 0."""
+        nz, mx, macs = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        r = lib().fcc_dct_radix2_stats(self.handle, int(level), ctypes.byref(nz), ctypes.byref(mx), ctypes.byref(macs))
+        if r < 0:
+            raise FccError(last_error(), "fcc_dct_radix2_stats")
+        return macs.value if level == 0 else (nz.value, mx.value, r)
 
     def check(self):
         """Synchronise and raise if a device-side wait of an earlier call timed out."""

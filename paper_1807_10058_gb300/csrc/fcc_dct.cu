@@ -26,6 +26,7 @@
 #include "mix_tiled.cuh"
 #include "pair.cuh"
 #include "plan.h"
+#include "radix2.h"
 
 using namespace fcc;
 
@@ -126,6 +127,7 @@ struct fcc_plan {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_host = nullptr;
     std::vector<void*> allocs;
     std::vector<int64_t> alloc_bytes;   // sizes of allocs (live-byte bookkeeping)
+    R2Plan* r2 = nullptr;               // set: the forward runs the radix-2 recursion (fcc_dct_plan_radix2)
     // chunked schedule: volumes per chunk and internal streams (fork / join
     // with the caller's stream through events)
     int64_t chunk_bytes = 32ll << 20;
@@ -388,6 +390,7 @@ void release(fcc_plan* p) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(p->device);
+    if (p->r2) r2_destroy(p->r2);
     for (void* a : p->allocs) cudaFree(a);
     for (int64_t b : p->alloc_bytes) g_live_dev_bytes -= b;
     --g_live_plans;
@@ -1408,6 +1411,16 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
     if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, which);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, which);
+    if (p->r2) {   // the radix-2 recursion: forward only
+        if (which != 0) return fail(FCC_ERR_UNSUPPORTED);
+        if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != p->device) cudaSetDevice(p->device);
+        const fcc_status s = r2_forward(p->r2, in, out, (cudaStream_t)stream);
+        if (cur != p->device) cudaSetDevice(cur);
+        return s == FCC_OK ? FCC_OK : fail(s);
+    }
     if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
     int cur = 0;
     if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
@@ -1422,6 +1435,7 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
 
 fcc_status dispatch_packed(fcc_plan* p, int which, const void* in, void* out, void* stream) {
     if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
     if (*(volatile int*)p->h_status != 0) {   // as in dispatch
         *(volatile int*)p->h_status = 0;
         return fail(FCC_ERR_TIMEOUT);
@@ -1489,6 +1503,7 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
 
 fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream, bool packed = false) {
     if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
+    if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
     if (which == 1 && !p->invertible) return fail(FCC_ERR_UNSUPPORTED);
     if (packed && packed_ok(p, which)) return fail(packed_ok(p, which));
     cudaStream_t st = (cudaStream_t)stream;
@@ -1621,6 +1636,37 @@ fcc_plan* fcc_dct_plan_skew(int order, int batch, int dtype, const int* v, int d
     return make_plan(std::vector<int>((size_t)batch, order), dtype, v, d);
 }
 
+fcc_plan* fcc_dct_plan_radix2(int order, int batch, int dtype, const int* v, int d) {
+    if ((dtype != FCC_C64 && dtype != FCC_C32) || !(order == 2 || order == 4 || order == 8 || order == 16) ||
+        batch < 1 || batch > 65535) {
+        fail(FCC_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    const int canon[3] = {1, 0, 3};
+    if (!v) { v = canon; d = 8; }
+    if (d < 1 || d > kMaxShiftDen) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    for (int i = 0; i < 3; ++i)
+        if (std::abs(v[i]) > kMaxShiftNum) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
+    fcc_plan* p = make_plan(std::vector<int>((size_t)batch, order), dtype, v, d);
+    if (!p) return nullptr;
+    fcc_status s = FCC_OK;
+    auto alloc = [](void* ctx, void** ptr, size_t bytes) -> fcc_status { return dev_alloc((fcc_plan*)ctx, ptr, bytes); };
+    p->r2 = r2_build(order, batch, dtype == FCC_C64, v, d, alloc, p, &s);
+    if (!p->r2) {
+        release(p);
+        fail(s);
+        return nullptr;
+    }
+    return p;
+}
+
+int fcc_dct_radix2_stats(const fcc_plan* p, int level, double* nnz_per_row, double* max_abs, double* macs_per_point) {
+    if (!p || !p->r2) { fail(FCC_ERR_INVALID_ARG); return -1; }
+    const int r = r2_stats(p->r2, level, nnz_per_row, max_abs, macs_per_point);
+    if (r < 0) fail(FCC_ERR_INVALID_ARG);
+    return r;
+}
+
 fcc_plan* fcc_dct_plan_ragged(const int* orders, int count, int dtype) {
     if (!orders || count < 1) { fail(FCC_ERR_INVALID_ARG); return nullptr; }
     return make_plan(std::vector<int>(orders, orders + count), dtype);
@@ -1669,6 +1715,7 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
 
 fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream, int reps, float* best_ms) {
     if (!p || !in || !out || reps < 1 || reps > 100) return fail(FCC_ERR_INVALID_ARG);
+    if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
     cudaStream_t st = (cudaStream_t)stream;
     struct Cand { int chunk_mb, streams, ragged, tc, fold; };
     std::vector<Cand> cands;
@@ -1780,6 +1827,7 @@ int64_t fcc_dct_out_bytes(const fcc_plan* p) { return p ? out_bytes(p, 0) : 0; }
 
 int fcc_dct_launches(const fcc_plan* p, int which) {
     if (!p) return 0;
+    if (p->r2) return which == 0 ? r2_launches(p->r2) : 0;
     if (which == 3 || which == 4) return packed_launches(p, which - 3);
     int total = 0;
     if (!is_double(p->dtype) && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_ok(p, which)) {
@@ -2025,7 +2073,7 @@ extern "C" fcc_status fcc_dct_inverse_static(fcc_plan* p, const void* in, void* 
     const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, 1);
     const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, 1);
     if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
-    if ((p->dtype != FCC_R32 && p->dtype != FCC_C32) || p->skew) return fail(FCC_ERR_UNSUPPORTED);
+    if ((p->dtype != FCC_R32 && p->dtype != FCC_C32) || p->skew || p->r2) return fail(FCC_ERR_UNSUPPORTED);
     for (int n : p->orders)
         if ((uint64_t)n * n * n * sizeof(float2) > FCC_STATIC_SCRATCH_BYTES) return fail(FCC_ERR_UNSUPPORTED);
     int cur = 0;

@@ -112,3 +112,13 @@ def test_injected_allocation_failure_of_the_plan_object():
     else:
         assert L.fcc_dct_last_error() != binding.FCC_ERR_ALLOC
     assert binding.allocations()[1] == plans0
+
+
+@pytest.mark.parametrize("order,dtype", [(32, 1), (6, 1), (0, 1), (8, 2), (8, 5)])
+def test_radix2_plan_arguments(order, dtype):
+    """The radix-2 recursion takes orders 2, 4, 8, 16 and complex dtypes only
+    (checked before touching the GPU)."""
+    L = binding.lib()
+    assert not L.fcc_dct_plan_radix2(order, 1, dtype, None, 8)
+    assert L.fcc_dct_last_error() == binding.FCC_ERR_INVALID_ARG
+    assert L.fcc_dct_radix2_stats(None, 0, None, None, None) == -1
