@@ -417,6 +417,19 @@ def secondary_configs(dev):
     r2["rel_diff_radix2_c32_vs_radix2_c64"] = (torch.linalg.vector_norm(y32.to(torch.complex128) - y64)
                                                / torch.linalg.vector_norm(y64)).item()
     out["radix2_n16_b64"] = r2
+    # the voxel rendering of Sec. 5 (Fig. 4): one n = 128 phantom volume drawn as
+    # cubes and as the FCC lattice's rhombic dodecahedra, 1024 x 1024 pixels
+    n = 128
+    vol = inputs.phantom_device(n, 1, seed=7, device=dev)
+    vol = (vol / vol.max()).clamp(0, 1)
+    img = torch.empty(1024 * 1024, device=dev)
+    ren = {"order": n, "pixels": 1024 * 1024, "step": 0.25, "kappa": 0.5}
+    for cells in ("cube", "rhombic_dodecahedron"):
+        fn = lambda: binding.render_cells(vol, n, cells, azimuth=0.6, elevation=0.4, kappa=0.5, step=0.25,
+                                          width=1024, height=1024, image=img)
+        ren[cells + "_ms"] = _time(fn, 5, 2)
+        ren[cells + "_mean_grey"] = img.mean().item()
+    out["render_n128_1024px"] = ren
     return out
 
 

@@ -86,6 +86,29 @@ typedef enum {
 fcc_plan* fcc_dct_plan(int order, int batch, int dtype);
 
 /*
+ * Rendering of voxel data as lattice cells (Sec. 5, Fig. 4; the paper shows
+ * figures only, this is a headless restatement): every data point of an n^3
+ * volume (device, FP32, [n][n][n], the layout of a real forward input) is
+ * drawn as the cell around its lattice point -- FCC_CELL_CUBE: the unit cube
+ * around (i, l, q) on the cubic lattice (Fig. 4a); FCC_CELL_RHOMBIC_DODECAHEDRON:
+ * the Voronoi cell of z = (i + q, i + l, l + q) in the FCC lattice
+ * D3 = {z in Z^3 : z1 + z2 + z3 even} (Fig. 4b) -- with the data value as
+ * opacity (clamped to [0, 1]; 0 invisible, 1 opaque).  An orthographic ray
+ * marcher looks at the centre of the cells' bounding box from the direction
+ * (cos e cos a, cos e sin a, sin e) (a = azimuth, e = elevation, radians),
+ * the width x height image spanning the box's bounding sphere; along each ray
+ * a sample every `step` (lattice units) inside a cell of value v has opacity
+ * 1 - exp(-kappa v step) and emits v, composited front to back.  Writes the
+ * grey level of every pixel to image[height][width] (device, FP32),
+ * asynchronously on `stream`.  FCC_ERR_INVALID_ARG for NULL pointers, n outside
+ * 1..FCC_MAX_ORDER, an unknown cell kind, sizes outside 1..16384, kappa or
+ * step not positive, or more than 10^6 steps per ray.
+ */
+typedef enum { FCC_CELL_CUBE = 0, FCC_CELL_RHOMBIC_DODECAHEDRON = 1 } fcc_cell;
+fcc_status fcc_render_cells(const float* volume, int n, int cells, float azimuth, float elevation, float kappa,
+                            float step, int width, int height, float* image, void* stream);
+
+/*
  * The paper's own fast algorithm (Sec. 4.B, eq. FastAlgorithm): the radix-2x2x2
  * factorisation
  *   DCT_n(c) = P_n . (sum over i in {0,1}^3 of DCT_m((c + i)/2)) . (DCT_2(c) (x) 1_{m^3}) . B_n(c),

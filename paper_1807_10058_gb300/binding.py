@@ -25,6 +25,7 @@ EXPORTS = [
     "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
     "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host", "fcc_dct_test_fail_alloc",
     "fcc_dct_test_allocations", "fcc_dct_plan_radix2", "fcc_dct_radix2_stats",
+    "fcc_render_cells",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -58,6 +59,9 @@ def lib():
         L.fcc_dct_radix2_stats.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]
         L.fcc_dct_radix2_stats.restype = i32
+        f32 = ctypes.c_float
+        L.fcc_render_cells.argtypes = [vp, i32, i32, f32, f32, f32, f32, i32, i32, vp, vp]
+        L.fcc_render_cells.restype = i32
         L.fcc_dct_describe_skew.argtypes = [i32, ctypes.POINTER(i32), i32, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                             ctypes.POINTER(i32), ctypes.POINTER(i32)] + [vp] * 7
         L.fcc_dct_describe_skew.restype = i32
@@ -150,6 +154,23 @@ def allocations():
     plans, dev = ctypes.c_int64(), ctypes.c_int64()
     seq = lib().fcc_dct_test_allocations(ctypes.byref(plans), ctypes.byref(dev))
     return seq, plans.value, dev.value
+
+
+CELLS = {"cube": 0, "rhombic_dodecahedron": 1}
+
+
+def render_cells(volume, n, cells="rhombic_dodecahedron", azimuth=0.6, elevation=0.4, kappa=4.0, step=0.05,
+                 width=256, height=256, image=None):
+    """Grey-level image of an n^3 FP32 device volume drawn as lattice cells
+    (fcc_render_cells): cubes or the rhombic dodecahedra of the FCC lattice."""
+    import torch
+    if image is None:
+        image = torch.empty(height * width, dtype=torch.float32, device=volume.device)
+    st = torch.cuda.current_stream(volume.device).cuda_stream
+    _check(lib().fcc_render_cells(ctypes.c_void_p(volume.data_ptr()), int(n), CELLS[cells], float(azimuth),
+                                  float(elevation), float(kappa), float(step), int(width), int(height),
+                                  ctypes.c_void_p(image.data_ptr()), ctypes.c_void_p(st)), "fcc_render_cells")
+    return image
 
 
 def weyl_group():
