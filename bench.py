@@ -543,7 +543,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
     ap.add_argument("--autotune", type=int, default=1, help="run fcc_dct_autotune before timing (1) or not (0)")
     ap.add_argument("--sched", default="",
-                    help="schedule keys applied after the autotuner, e.g. 'tc_ws=0,streams=1'")
+                    help="schedule keys applied after the autotuner, e.g. 'streams=1,chunk_mb=32'")
     ap.add_argument("--output", default="complex", choices=["complex", "packed"],
                     help="forward output: complex64 point values, or the Hermitian-packed reals of real plans")
     args = ap.parse_args()

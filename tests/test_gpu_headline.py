@@ -126,3 +126,27 @@ def test_headline_inverse_and_adjoint_whole_volumes(headline, dtype):
             av = ad[v * N ** 3:(v + 1) * N ** 3].cpu().numpy().astype(np.float64)
             aref = oracle.adjoint_sum_fft(gh[v].astype(np.complex128).reshape(N, N, N), N).real.reshape(-1)
             _check_volume(av, aref, REL[dtype], ELEM[dtype], (dtype, v, "adjoint"))
+
+
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32"])
+def test_order_96_whole_volumes(dtype):
+    """Order 96 (the gradient-descent configuration's order and the top of the
+    ragged range; register-radix shape 24 x 4): two whole volumes of a batch
+    of 8 phantoms against the oracle, forward, and the inverse residual."""
+    n, batch = 96, 8
+    vols = {v: inputs.phantom(n, 1, seed=700 + v)[0].astype(np.float32) for v in (0, 5)}
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(96)
+    x = torch.rand(batch * n ** 3, generator=gen, device=DEV, dtype=torch.float32)
+    for v, vol in vols.items():
+        x[v * n ** 3:(v + 1) * n ** 3] = torch.from_numpy(vol.reshape(-1)).to(DEV)
+    with binding.Plan(n, batch, dtype) as p:
+        y = p.forward(x)
+        xi = p.inverse(y)
+        p.check()
+        for v, vol in vols.items():
+            ref = oracle.forward_sum_fft(vol.astype(np.float64), n)
+            got = y[v * n ** 3:(v + 1) * n ** 3].cpu().numpy().astype(np.complex128)
+            assert _rel(got, ref.reshape(-1)) < REL[dtype], (dtype, v)
+            back = xi[v * n ** 3:(v + 1) * n ** 3].cpu().numpy().astype(np.float64)
+            assert _rel(back, vol.reshape(-1).astype(np.float64)) < 4 * REL["r32"], (dtype, v)
