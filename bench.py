@@ -93,13 +93,12 @@ def kernel_sources_digest():
     csrc = os.path.join(ROOT, "paper_1807_10058_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(TRAFFIC_KERNEL_SOURCES):
-        if True:
-            with open(os.path.join(csrc, name)) as f:
-                code = f.read()
-            code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
-            code = re.sub(r"//[^\n]*", " ", code)
-            h.update(name.encode())
-            h.update(" ".join(code.split()).encode())
+        with open(os.path.join(csrc, name)) as f:
+            code = f.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(name.encode())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()
 
 

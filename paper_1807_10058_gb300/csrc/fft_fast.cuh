@@ -105,6 +105,59 @@ __device__ __forceinline__ void pencil_stage1(float* vr, float* vi, int j, float
     for (int k2 = 0; k2 < R1; ++k2) ex[j * (R1 + 1) + k2] = make_float2(vr[k2], vi[k2]);
 }
 
+// Order 128 (R1 = 16, G = 8): stage 1 of thread j with the exchange done by
+// warp shuffles instead of shared memory.  The 8 threads of a pencil are
+// lanes j * lstride + c; thread j holds A[j][k2] (k2 < 16) after the
+// length-16 DFT and the twiddle.  Viewing (A[j][e], A[j][e + 8]) as element
+// (j, e) of an 8 x 8 matrix, three butterfly stages (lane distance m lstride,
+// m = 1, 2, 4) transpose it: at stage m, of each position pair (e, e | m)
+// the thread whose bit m of j is set keeps e | m and sends e, the other keeps
+// e and sends e | m.  Afterwards thread q holds (ur[0][jj], ur[1][jj]) =
+// (A[jj][q], A[jj][q + 8]), the inputs of its two length-8 DFTs.
+template <int S>
+__device__ __forceinline__ void pencil128_stage1_shfl(float (&vr)[16], float (&vi)[16], int j, int lstride,
+                                                      const float2* tw, float (&ur)[2][8], float (&ui)[2][8]) {
+    reg::Dft<16, S, float>::run(vr, vi);
+#pragma unroll
+    for (int k2 = 1; k2 < 16; ++k2) {
+        const float2 w = tw[(j * k2) & 127];
+        const float wi = S > 0 ? w.y : -w.y;
+        const float t = vr[k2] * w.x - vi[k2] * wi;
+        vi[k2] = vr[k2] * wi + vi[k2] * w.x;
+        vr[k2] = t;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        ur[0][e] = vr[e];
+        ui[0][e] = vi[e];
+        ur[1][e] = vr[e + 8];
+        ui[1][e] = vi[e + 8];
+    }
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+        const bool hi = (j & m) != 0;
+#pragma unroll
+        for (int e0 = 0; e0 < 8; ++e0) {
+            if (e0 & m) continue;
+            const int e1 = e0 | m;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float sr = hi ? ur[h][e0] : ur[h][e1];
+                float si = hi ? ui[h][e0] : ui[h][e1];
+                sr = __shfl_xor_sync(0xffffffffu, sr, m * lstride);
+                si = __shfl_xor_sync(0xffffffffu, si, m * lstride);
+                if (hi) {
+                    ur[h][e0] = sr;
+                    ui[h][e0] = si;
+                } else {
+                    ur[h][e1] = sr;
+                    ui[h][e1] = si;
+                }
+            }
+        }
+    }
+}
+
 template <int N, int S>
 struct PencilFft {
     using L = FastLayout<N>;
@@ -515,18 +568,23 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
                 vi[m] = t.y;
             }
         }
-        pencil_stage1<N, 1>(vr, vi, j, ex, tw);
-        __syncwarp();
+        if constexpr (N == 128) {
+            static_assert(R1 == 16 && G == 8 && PPW == 4, "order-128 shuffle exchange");
+            pencil128_stage1_shfl<1>(vr, vi, j, PPW, tw, ur, ui);   // exchange by warp shuffles
+        } else {
+            pencil_stage1<N, 1>(vr, vi, j, ex, tw);
+            __syncwarp();
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
+            for (int e = 0; e < E; ++e) {
 #pragma unroll
-            for (int jj = 0; jj < G; ++jj) {
-                const float2 t = ex[jj * (R1 + 1) + j + G * e];
-                ur[e][jj] = t.x;
-                ui[e][jj] = t.y;
+                for (int jj = 0; jj < G; ++jj) {
+                    const float2 t = ex[jj * (R1 + 1) + j + G * e];
+                    ur[e][jj] = t.x;
+                    ui[e][jj] = t.y;
+                }
             }
+            __syncwarp();
         }
-        __syncwarp();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             reg::Dft<G, 1, float>::run(ur[e], ui[e]);
