@@ -557,10 +557,11 @@ struct ProfScope {
 
 template <typename T>
 fcc_status launch_fft(const OrderTables& t, const T* in, T* out, int64_t nvol, int axis, int sign,
-                      cudaStream_t st) {
+                      cudaStream_t st, int64_t vstride = 0) {
     const int n = t.n;
-    if (n == 1) {
-        if (in != out) cudaMemcpyAsync(out, in, nvol * 2 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    if (n == 1) {   // the identity
+        const size_t pitch = (size_t)(vstride > 1 ? vstride : 1) * 2 * sizeof(T);
+        if (in != out) cudaMemcpy2DAsync(out, pitch, in, pitch, 2 * sizeof(T), (size_t)nvol, cudaMemcpyDeviceToDevice, st);
         return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
     }
     FftArgs a{};
@@ -572,6 +573,7 @@ fcc_status launch_fft(const OrderTables& t, const T* in, T* out, int64_t nvol, i
     a.P = std::max(1, budget / n);
     if (axis != 2) a.P = std::min(a.P, n);
     a.nvol = nvol;
+    a.vstride = vstride > 0 ? vstride : (int64_t)n * n * n;
     a.sign = sign;
     int64_t tiles;
     if (axis == 2) tiles = (nvol * n * n + a.P - 1) / a.P;
@@ -754,17 +756,10 @@ fcc_status launch_dft3(const OrderTables& t, int sign, const float* in, float* o
         if ((s = fast_fft(t.n, false, sign, (const float2*)in, (float2*)out, nvol, tw, vstride, st))) return s;
         return fast_fft(t.n, true, sign, (const float2*)out, (float2*)out, nvol, tw, vstride, st);
     }
-    // generic passes work on contiguous volumes: one launch set per volume when strided
-    fcc_status s = FCC_OK;
-    const int64_t step = vstride == n3 ? nvol : 1;
-    for (int64_t v = 0; v < nvol && !s; v += step) {
-        const int64_t nv = std::min(step, nvol - v);
-        const float* src = in + 2 * v * vstride;
-        float* dst = out + 2 * v * vstride;
-        s = launch_fft<float>(t, src, dst, nv, 0, sign, st);
-        if (!s) s = launch_fft<float>(t, dst, dst, nv, 1, sign, st);
-        if (!s) s = launch_fft<float>(t, dst, dst, nv, 2, sign, st);
-    }
+    // generic passes: one launch per axis over every (possibly strided) volume
+    fcc_status s = launch_fft<float>(t, in, out, nvol, 0, sign, st, vstride);
+    if (!s) s = launch_fft<float>(t, out, out, nvol, 1, sign, st, vstride);
+    if (!s) s = launch_fft<float>(t, out, out, nvol, 2, sign, st, vstride);
     return s;
 }
 
@@ -1536,11 +1531,14 @@ fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, vo
 }
 
 // Launches of one run of `nv` volumes of order n (run_group, excluding the
-// ragged fast paths).
+// ragged fast paths).  Every grid with one row per volume (or pair) is split
+// into launches of at most 65,535 rows.
+int64_t grid_rows(int64_t rows) { return (rows + 65534) / 65535; }
+
 int group_launches(const fcc_plan* p, int which, int n, int64_t nv) {
-    int total = 0;
+    int64_t total = 0;
     const int64_t n3 = (int64_t)n * n * n;
-    const int mix = (int)((nv + 65534) / 65535);
+    const int fft = n > 1 ? 3 : 0;   // order 1: the DFT is a copy, no kernel
     if (!is_double(p->dtype) && n > 1 && p->skew) {
         // run_group_skew: per chunk the mixing launches (free and boundary
         // tiles, or the generic kernel) and the DFT passes; the forward
@@ -1550,37 +1548,43 @@ int group_launches(const fcc_plan* p, int which, int n, int64_t nv) {
         const bool tiled = skew_tiled(tb);
         const bool split_b = which == 0 && tiled && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles;
         const int kinds = !tiled ? 1 : split_b ? 1 : (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
-        if (split_b) total += mix;
+        if (split_b) total += grid_rows(nv);
         const int64_t cv = which == 0 ? chunk_vols(p, n) : std::max<int64_t>(1, p->scratch_points / n3);
-        for (int64_t v0 = 0; v0 < nv; v0 += cv)
-            total += kinds * (int)((std::min(cv, nv - v0) + 65534) / 65535) + dft;
+        for (int64_t v0 = 0; v0 < nv; v0 += cv) total += kinds * grid_rows(std::min(cv, nv - v0)) + dft;
     } else if (!is_double(p->dtype) && n > 1) {
+        // run_group_fast
         const int64_t cv = std::min<int64_t>(chunk_vols(p, n), std::max<int64_t>(1, p->scratch_points / n3));
-        const int dft = has_fast_fft(n) ? 2 : 3;
+        const bool fast = has_fast_fft(n);
         const OrderTables& tb = p->tabs.at(n);
         const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
         const bool pairing = is_real_in(p->dtype) && p->pairing && nv >= 2;
-        const bool tc_all = is_tc(p->dtype) && tb.tc_core_image;   // one launch mixes every tile
+        const bool tc = is_tc(p->dtype), tc_all = tc && tb.tc_core_image;   // one launch mixes every tile
         const int64_t npairs = pairing ? nv / 2 : 0;
-        // per paired chunk: mixing, then the DFT passes and the pair split /
-        // merge (the fast forward fuses the split into its pencil pass;
-        // generic passes over strided pairs go pair by pair)
         const bool split_b = which == 0 && npairs > 0 && tb.free_tiles > 0 && tb.ntiles > tb.free_tiles && !tc_all;
-        if (split_b) total += 1;
+        if (split_b) total += grid_rows(npairs);   // the boundary tiles of every pair
         for (int64_t p0 = 0; p0 < npairs; p0 += cv) {
-            const int64_t np = std::min(cv, npairs - p0);
-            // (the inverse / adjoint merge into a compact workspace first)
-            const int64_t dft_pair = has_fast_fft(n) ? 2 : (which == 0 ? 3 * np + 1 : 4);
-            total += (int)((split_b || tc_all ? 1 : mixl) + dft_pair);
+            const int64_t np = std::min(cv, npairs - p0), rows = grid_rows(np);
+            if (which == 0) {
+                // mixing (tensor cores: one kernel; else free (+ boundary) tiles),
+                // then slab + pencil-with-split, or three passes + the split kernel
+                total += (tc ? 1 : split_b ? 1 : mixl) * rows;
+                total += fast ? 2 : 3 + rows;
+            } else {
+                // merge fused into the pencil pass + slab, or merge + three passes;
+                // then the mixing
+                total += fast ? 2 : rows + 3;
+                total += (tc_all ? 1 : mixl) * rows;
+            }
         }
         const int64_t rest = nv - 2 * npairs;
-        total += (int)(((rest + cv - 1) / cv) * (mixl + dft));
-    } else if (which == 0) total += mix + 3;
-    else {
+        for (int64_t v0 = 0; v0 < rest; v0 += cv) total += mixl * grid_rows(std::min(cv, rest - v0)) + (fast ? 2 : 3);
+    } else if (which == 0) {
+        total += grid_rows(nv) + fft;
+    } else {
         const int64_t chunk = std::max<int64_t>(1, p->scratch_points / n3);
-        total += (int)((nv + chunk - 1) / chunk) * 4;
+        for (int64_t v0 = 0; v0 < nv; v0 += chunk) total += fft + grid_rows(std::min(chunk, nv - v0));
     }
-    return total;
+    return (int)std::min<int64_t>(total, 0x7fffffff);
 }
 
 // Launches of the packed forward (which 0) / inverse (1): run_group_packed.
@@ -1599,9 +1603,9 @@ int packed_launches(const fcc_plan* p, int which) {
             const OrderTables& tb = p->tabs.at(n);
             const int mixl = (tb.free_tiles > 0 ? 1 : 0) + (tb.ntiles > tb.free_tiles ? 1 : 0);
             const bool tc = is_tc(p->dtype), tc_all = tc && tb.tc_core_image;
-            const int per_chunk = (which == 0 ? (tc ? 1 : mixl) : (tc_all ? 1 : mixl)) + 2;
+            const int mix = which == 0 ? (tc ? 1 : mixl) : (tc_all ? 1 : mixl);
             const int64_t npairs = nv / 2, cp = packed_pairs_per_chunk(p, n);
-            total += (int)((npairs + cp - 1) / cp) * per_chunk;
+            for (int64_t p0 = 0; p0 < npairs; p0 += cp) total += mix * (int)grid_rows(std::min(cp, npairs - p0)) + 2;
             v0 = 2 * npairs;
         }
         const int64_t cv = std::max<int64_t>(1, packed_slot_of(p) * packed_streams_of(p) / n3);

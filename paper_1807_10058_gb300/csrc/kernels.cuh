@@ -148,8 +148,8 @@ struct FftArgs {
     int axis;      // 0: slowest (stride n^2), 1: middle (stride n), 2: fastest
     int P;         // pencils per block
     int64_t nvol;
+    int64_t vstride;   // complex values from one volume to the next (>= n^3)
     int sign;      // +1 or -1
-    int64_t tiles_per_vol;
 };
 
 template <typename T>
@@ -232,7 +232,8 @@ __device__ __forceinline__ int64_t fft_global_index(const FftArgs& a, int64_t ti
     if (a.axis == 2) {
         const int64_t row = tile * a.P + p;
         ok = row < a.nvol * n2;
-        return row * n + e;
+        const int64_t vol = row / n2;
+        return vol * a.vstride + (row - vol * n2) * n + e;
     }
     const int ctiles = (n + a.P - 1) / a.P;
     const int64_t vol = tile / ((int64_t)n * ctiles);
@@ -240,8 +241,8 @@ __device__ __forceinline__ int64_t fft_global_index(const FftArgs& a, int64_t ti
     const int fixed = (int)(rem / ctiles);
     const int c = (int)(rem % ctiles) * a.P + p;
     ok = c < n;
-    if (a.axis == 1) return ((vol * n + fixed) * n + e) * n + c;
-    return ((vol * n + e) * n + fixed) * n + c;
+    if (a.axis == 1) return vol * a.vstride + ((int64_t)fixed * n + e) * n + c;
+    return vol * a.vstride + ((int64_t)e * n + fixed) * n + c;
 }
 
 template <typename T>
