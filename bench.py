@@ -274,6 +274,43 @@ def evaluate_probes(probes):
     return out
 
 
+WHOLE_FORMS = ("r32", "r32_bf16x3", "r32_tf32x3", "r32_bf16x6")
+
+
+def whole_volume_outputs(x, n, dev):
+    """Volume 0 of the bench input through every form (a plan over the first
+    pair of volumes), for the whole-volume comparison of the CPU leg."""
+    from paper_1807_10058_gb300 import binding
+    n3 = n ** 3
+    outs = {}
+    for form in WHOLE_FORMS:
+        with binding.Plan(n, 2, form) as q:
+            outs[form] = q.forward(x[:2 * n3])[:n3].cpu().numpy()
+    return {"vol": x[:n3].double().cpu().numpy(), "n": n, "outs": outs}
+
+
+def evaluate_whole_volume(w):
+    """CPU leg: every output of volume 0 against the oracle's FP64 exchanged-sum
+    form (orbit sums, then numpy's FFT): relative L2 and largest error over the
+    output RMS, element by element over the whole volume."""
+    import numpy as np
+    import oracle
+    try:
+        t0 = time.perf_counter()
+        ref = oracle.forward_sum_fft(w["vol"], w["n"]).ravel()
+        dt = time.perf_counter() - t0
+        rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+        forms = {}
+        for form, got in w["outs"].items():
+            err = np.abs(got.astype(np.complex128) - ref)
+            forms[form] = {"rel_l2": float(np.linalg.norm(err) / np.linalg.norm(ref)),
+                           "max_err_over_rms": float(err.max() / rms)}
+        return {"oracle": "FP64 exchanged-sum form (orbit sums + FFT), whole volume 0 (%d points, %.1f s)"
+                          % (ref.size, dt), "forms": forms}
+    except Exception as exc:  # accuracy is reported, never required
+        return {"error": str(exc)}
+
+
 def _time(fn, steps, warmup):
     import torch
     for _ in range(warmup):
@@ -649,8 +686,11 @@ def main():
     if packed:   # the packed values are the complex output re-laid out
         plan.forward(x, out=y)
         relayout = packed_vs_complex(pk, y, n, batch, dev)
+    whole = None
     if rank == 0:
         probes["headline"] = sampled_accuracy(x, y, n, dev)
+        if world == 1 and not args.no_cpu_baseline and batch >= 2:
+            whole = whole_volume_outputs(x, n, dev)
 
     # end to end through the C ABI with host buffers
     xh = x.cpu().pin_memory()
@@ -708,6 +748,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n)
         acc = evaluate_probes(probes)
+        if whole is not None:
+            whole = evaluate_whole_volume(whole)
     if compare is not None and "compare" in acc:
         compare["accuracy"] = acc["compare"]
     if extra and "skew" in acc:
@@ -751,6 +793,7 @@ def main():
             "gpu_launches": plan.launches(3 if packed else 0) * args.steps,
             "clocks": ck,
             "accuracy": accuracy,
+            "accuracy_whole_volume": whole if whole is None or "outs" not in whole else None,
             "compare": compare,
             "secondary": extra,
             "cpu_baseline": cpu,

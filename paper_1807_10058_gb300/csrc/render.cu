@@ -43,7 +43,39 @@ __global__ void render_kernel(const float* __restrict__ vol, int n, int cells, C
                                  cam.o.z + sx * cam.right.z + sy * cam.up.z);
     float C = 0.f, A = 0.f;
     const int nsteps = (int)(cam.t1 / step);
-    for (int s = 0; s < nsteps && A < 0.999f; ++s) {
+    // clip the ray to the occupied region (samples outside it hit no cell):
+    // in voxel coordinates u = (i, l, q) -- the lattice coordinates x
+    // themselves for cubes, u = B^{-1} x for the FCC lattice -- every sample
+    // that decodes to a voxel of the volume lies in lo <= u_a <= hi (cubes:
+    // [-1/2, n - 1/2]; a rhombic dodecahedron reaches at most 3/4 from its
+    // centre in each voxel coordinate, so [-3/2, n + 1/2] keeps a margin)
+    float t_in = 0.f, t_out = cam.t1;
+    {
+        const float lo = cells == FCC_CELL_CUBE ? -0.5f : -1.5f;
+        const float hi = cells == FCC_CELL_CUBE ? (float)n - 0.5f : (float)n + 0.5f;
+        float uo[3], ud[3];
+        if (cells == FCC_CELL_CUBE) {
+            uo[0] = o.x; uo[1] = o.y; uo[2] = o.z;
+            ud[0] = cam.dir.x; ud[1] = cam.dir.y; ud[2] = cam.dir.z;
+        } else {   // i = (z1 + z2 - z3) / 2, l = (z2 + z3 - z1) / 2, q = (z1 + z3 - z2) / 2
+            uo[0] = 0.5f * (o.x + o.y - o.z); uo[1] = 0.5f * (o.y + o.z - o.x); uo[2] = 0.5f * (o.x + o.z - o.y);
+            ud[0] = 0.5f * (cam.dir.x + cam.dir.y - cam.dir.z); ud[1] = 0.5f * (cam.dir.y + cam.dir.z - cam.dir.x);
+            ud[2] = 0.5f * (cam.dir.x + cam.dir.z - cam.dir.y);
+        }
+        for (int a = 0; a < 3; ++a) {
+            if (fabsf(ud[a]) < 1e-12f) {
+                if (uo[a] < lo || uo[a] > hi) t_out = -1.f;   // parallel and outside
+            } else {
+                const float ta = (lo - uo[a]) / ud[a], tb = (hi - uo[a]) / ud[a];
+                t_in = fmaxf(t_in, fminf(ta, tb));
+                t_out = fminf(t_out, fmaxf(ta, tb));
+            }
+        }
+    }
+    // sample s sits at t = (s + 1/2) step; one sample of slack on each side
+    const int s0 = t_out < t_in ? nsteps : max(0, (int)floorf(t_in / step - 0.5f) - 1);
+    const int s1 = t_out < t_in ? 0 : min(nsteps, (int)ceilf(t_out / step - 0.5f) + 2);
+    for (int s = s0; s < s1 && A < 0.999f; ++s) {
         const float t = (s + 0.5f) * step;
         const float x[3] = {o.x + t * cam.dir.x, o.y + t * cam.dir.y, o.z + t * cam.dir.z};
         int i, l, q;

@@ -56,16 +56,25 @@ def render_numpy(vol, n, cells, az, el, kappa, step, W, H):
     return C
 
 
+# views: oblique, along an axis (rays parallel to two faces of the box the
+# kernel clips them to), along a body diagonal, from below
+VIEWS = [(0.7, 0.35), (0.0, 0.0), (np.pi / 4, 0.6154797), (2.5, -0.8)]
+
+
+@pytest.mark.parametrize("view", VIEWS)
 @pytest.mark.parametrize("cells", ["cube", "rhombic_dodecahedron"])
-def test_render_matches_numpy_restatement(cells):
+def test_render_matches_numpy_restatement(cells, view):
+    """The kernel marches each ray only through the region its cells can
+    occupy; the restatement marches the whole bounding sphere."""
+    az, el = view
     n, W, H = 8, 48, 40
     vol = inputs.phantom(n, 1, seed=3)[0]
     vol = np.clip(vol / max(vol.max(), 1e-9), 0, 1)
     vol[vol < 0.2] = 0.0
     x = torch.from_numpy(vol.astype(np.float32).reshape(-1)).to(DEV)
-    img = binding.render_cells(x, n, cells, azimuth=0.7, elevation=0.35, kappa=3.0, step=0.05, width=W, height=H)
+    img = binding.render_cells(x, n, cells, azimuth=az, elevation=el, kappa=3.0, step=0.05, width=W, height=H)
     got = img.cpu().numpy().reshape(H, W)
-    want = render_numpy(vol.astype(np.float32).astype(np.float64), n, cells, 0.7, 0.35, 3.0, 0.05, W, H)
+    want = render_numpy(vol.astype(np.float32).astype(np.float64), n, cells, az, el, 3.0, 0.05, W, H)
     diff = np.abs(got - want)
     # a sample within rounding distance of a cell face may land in the
     # neighbouring cell on one side only: a few pixels may differ
