@@ -239,6 +239,11 @@ int64_t fcc_dct_out_bytes(const fcc_plan* plan);
 int fcc_dct_launches(const fcc_plan* plan, int which /* 0 fwd, 1 inv, 2 adj, 3 fwd packed, 4 inv packed */);
 
 /*
+ * Tracing: every entry-point call and every kernel launch it makes open an
+ * NVTX range (host side; named after the call, e.g. "fcc_dct_forward", and
+ * after the kernel kind, e.g. "mix_tc_fwd", "fft_slab"), for timeline tools.
+ * Without a tool attached the ranges cost a function-pointer check.
+ *
  * Optional per-kernel timing.  When enabled, every kernel launch the plan
  * enqueues is bracketed by a pair of CUDA events on the launch stream.
  * fcc_dct_profile_read() waits for the recorded events, then writes for up
@@ -372,6 +377,15 @@ int fcc_dct_get_schedule(const fcc_plan* plan, int key);
  * `reps` (1..100) timed calls each, keeps the fastest and writes its time per
  * call to *best_ms (if not NULL).  Synchronises `stream`; overwrites `out`.
  * Candidates the device refuses are skipped.
+ *
+ * Cache: when the environment variable FCC_AUTOTUNE_CACHE names a file, the
+ * result is appended to it as one JSON object per line, keyed by the order
+ * (ragged plans: a hash of the order list), batch, dtype, shift and GPU name;
+ * a later call for the same key applies the cached schedule, times it with
+ * `reps` calls for *best_ms and skips the search (a cached schedule the
+ * device refuses is searched again).  The file is advisory: if it is
+ * missing, unreadable or malformed the search runs, and a failed write is
+ * ignored.
  */
 fcc_status fcc_dct_autotune(fcc_plan* plan, const void* in, void* out, void* stream, int reps, float* best_ms);
 

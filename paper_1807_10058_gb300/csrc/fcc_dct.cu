@@ -4,6 +4,7 @@
 // tensor-core mixing: mix_tc.cuh, mix_tc_inv.cuh; register-radix DFT passes:
 // fft_fast.cuh; pairing: pair.cuh; persistent ragged launch: ragged.cu).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -13,6 +14,7 @@
 #include <memory>
 #include <new>
 #include <numeric>
+#include <cstdio>
 #include <cstdlib>
 #include <string>
 #include <vector>
@@ -535,11 +537,15 @@ cudaEvent_t take_event(fcc_plan* p) {
     return e;
 }
 
+// Every launch site opens one: an NVTX range named after the kernel (host
+// side, for timeline tools; free without one attached) and, while the plan's
+// profiling is on, a pair of events around the launch.
 struct ProfScope {
     fcc_plan* p;
     fcc_plan::Rec r{nullptr, nullptr, nullptr};
     cudaStream_t st;
     ProfScope(const char* name, cudaStream_t s) : p(g_prof_plan), st(s) {
+        nvtxRangePushA(name);
         if (!p || !p->profiling) { p = nullptr; return; }
         r.name = name;
         r.a = take_event(p);
@@ -547,10 +553,17 @@ struct ProfScope {
         if (r.a) cudaEventRecord(r.a, st);
     }
     ~ProfScope() {
+        nvtxRangePop();
         if (!p) return;
         if (r.b) cudaEventRecord(r.b, st);
         p->recs.push_back(r);
     }
+};
+
+// NVTX range around one entry-point call (the transform's stages nest inside).
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
 };
 
 // --- launches -------------------------------------------------------------
@@ -1395,6 +1408,8 @@ fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t
 }
 
 fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* stream) {
+    static const char* names[3] = {"fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint"};
+    CallRange range(names[which < 0 || which > 2 ? 0 : which]);
     if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
     // a device-side timeout of an earlier call surfaces here (the word is
     // host memory; a call still running may set it later)
@@ -1429,6 +1444,7 @@ fcc_status dispatch(fcc_plan* p, int which, const void* in, void* out, void* str
 }
 
 fcc_status dispatch_packed(fcc_plan* p, int which, const void* in, void* out, void* stream) {
+    CallRange range(which == 0 ? "fcc_dct_forward_packed" : "fcc_dct_inverse_packed");
     if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
     if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
     if (*(volatile int*)p->h_status != 0) {   // as in dispatch
@@ -1497,6 +1513,7 @@ fcc_status run_host_pipelined(fcc_plan* p, int which, const char* hin, char* hou
 }
 
 fcc_status dispatch_host(fcc_plan* p, int which, const void* hin, void* hout, void* stream, bool packed = false) {
+    CallRange range(packed ? "fcc_dct_packed_host" : "fcc_dct_host");
     if (!p || !hin || !hout) return fail(FCC_ERR_INVALID_ARG);
     if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
     if (which == 1 && !p->invertible) return fail(FCC_ERR_UNSUPPORTED);
@@ -1717,10 +1734,93 @@ int fcc_dct_get_schedule(const fcc_plan* p, int key) {
     }
 }
 
+namespace {
+
+// The autotuner's cache: one JSON object per line in the file named by
+// FCC_AUTOTUNE_CACHE, keyed by the plan's shape, dtype, shift and GPU name;
+// a later line for the same key overrides an earlier one.  Reading and
+// writing it are advisory: a missing, unreadable or malformed file only
+// means that the search runs.
+std::string autotune_key(const fcc_plan* p) {
+    char gpu[256] = "unknown";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) {
+        std::snprintf(gpu, sizeof gpu, "%s", prop.name);
+        for (char* c = gpu; *c; ++c)
+            if (*c == '"' || *c == '\\') *c = '_';
+    } else {
+        cudaGetLastError();
+    }
+    std::string shape;
+    if (p->uniform) {
+        shape = "order=" + std::to_string(p->orders[0]);
+    } else {   // ragged: the order list, hashed (FNV-1a)
+        uint64_t h = 1469598103934665603ull;
+        for (int o : p->orders) {
+            h ^= (uint64_t)o;
+            h *= 1099511628211ull;
+        }
+        char buf[64];
+        std::snprintf(buf, sizeof buf, "ragged=%016llx", (unsigned long long)h);
+        shape = buf;
+    }
+    char key[512];
+    std::snprintf(key, sizeof key, "%s batch=%d dtype=%d shift=%d,%d,%d/%d gpu=%s", shape.c_str(), p->batch, p->dtype,
+                  p->shift_v[0], p->shift_v[1], p->shift_v[2], p->shift_d, gpu);
+    return key;
+}
+
+int json_int(const char* line, const char* name, bool& ok) {
+    const std::string pat = std::string("\"") + name + "\": ";
+    const char* at = std::strstr(line, pat.c_str());
+    int v = 0;
+    if (!at || std::sscanf(at + pat.size(), "%d", &v) != 1) ok = false;
+    return v;
+}
+
+// The cached schedule {chunk_mb, streams, ragged, tc_blocks, tc_fold} of `key`.
+bool autotune_cache_read(const char* path, const std::string& key, int sched[5]) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    bool found = false;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        if (!std::strstr(line, pat.c_str())) continue;
+        bool ok = true;
+        int s[5] = {json_int(line, "chunk_mb", ok), json_int(line, "streams", ok), json_int(line, "ragged", ok),
+                    json_int(line, "tc_blocks", ok), json_int(line, "tc_fold", ok)};
+        if (ok && s[0] >= 1 && s[0] <= 4096 && s[1] >= 1 && s[1] <= kMaxStreams && s[2] >= 0 && s[2] <= 2 &&
+            s[3] >= 0 && s[3] <= 8 && (s[4] == 0 || s[4] == 1)) {
+            std::memcpy(sched, s, sizeof s);
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void autotune_cache_write(const char* path, const std::string& key, const int sched[5], float ms) {
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"chunk_mb\": %d, \"streams\": %d, \"ragged\": %d, \"tc_blocks\": %d, "
+                 "\"tc_fold\": %d, \"ms\": %.4f}\n",
+                 key.c_str(), sched[0], sched[1], sched[2], sched[3], sched[4], (double)ms);
+    std::fclose(f);
+}
+
+}  // namespace
+
 fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream, int reps, float* best_ms) {
     if (!p || !in || !out || reps < 1 || reps > 100) return fail(FCC_ERR_INVALID_ARG);
     if (p->r2) return fail(FCC_ERR_UNSUPPORTED);
+    CallRange range("fcc_dct_autotune");
     cudaStream_t st = (cudaStream_t)stream;
+    const char* cache = std::getenv("FCC_AUTOTUNE_CACHE");
+    const std::string key = cache && *cache ? autotune_key(p) : std::string();
+    int cached[5];
+    const bool hit = !key.empty() && autotune_cache_read(cache, key, cached);
     struct Cand { int chunk_mb, streams, ragged, tc, fold; };
     std::vector<Cand> cands;
     const int tc0 = p->tc_blocks, f0 = p->tc_fold;
@@ -1770,6 +1870,18 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
     };
     Cand best = saved;
     float best_t = -1.f;
+    if (hit) {   // the cached schedule, timed once so that *best_ms is this call's
+        const Cand c = {cached[0], cached[1], cached[2], cached[3], cached[4]};
+        float ms = 0.f;
+        if (time_it(c, ms)) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            apply(c);
+            if (best_ms) *best_ms = ms;
+            return FCC_OK;
+        }
+        cands.insert(cands.begin(), c);   // refused here: search as if not cached
+    }
     for (const Cand& c : cands) {
         float ms = 0.f;
         if (time_it(c, ms) && (best_t < 0.f || ms < best_t)) {
@@ -1807,6 +1919,10 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
     }
     apply(best);
     if (best_ms) *best_ms = best_t;
+    if (!key.empty()) {
+        const int sched[5] = {best.chunk_mb, best.streams, best.ragged, best.tc, best.fold};
+        autotune_cache_write(cache, key, sched, best_t);
+    }
     return FCC_OK;
 }
 

@@ -123,6 +123,41 @@ def test_autotune_keeps_a_valid_schedule(ragged):
         assert rel(y, y0) < 1e-6
 
 
+def test_autotune_cache_round_trip(tmp_path, monkeypatch):
+    """FCC_AUTOTUNE_CACHE: the first search appends its result as a JSON line;
+    a plan of the same key takes the cached schedule without a search (no new
+    line); another key searches and appends; malformed lines are skipped."""
+    import json
+    cache = tmp_path / "autotune.jsonl"
+    monkeypatch.setenv("FCC_AUTOTUNE_CACHE", str(cache))
+    n, batch = 24, 6
+    flat = inputs.smoothed_noise(n, batch, seed=8).reshape(-1).astype(np.float32)
+    x = torch.from_numpy(flat).to(DEV)
+    out = torch.empty(n ** 3 * batch, dtype=torch.complex64, device=DEV)
+    with binding.Plan(n, batch, "r32") as p:
+        y0 = p.forward(x).cpu().numpy()
+        ms, sched = p.autotune(x, out, reps=2)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1, lines
+    rec = json.loads(lines[0])
+    assert "order=24 batch=6 dtype=" in rec["key"] and "gpu=" in rec["key"], rec
+    assert (rec["chunk_mb"], rec["streams"], rec["ragged"]) == (sched["chunk_mb"], sched["streams"], sched["ragged"])
+    with binding.Plan(n, batch, "r32") as q:
+        # a different schedule first: the cached one must replace it
+        q.set_schedule(chunk_mb=sched["chunk_mb"] + 7, streams=1 if sched["streams"] != 1 else 2)
+        ms2, sched2 = q.autotune(x, out, reps=2)
+        assert ms2 > 0 and sched2 == sched, (sched2, sched)
+        assert rel(q.forward(x).cpu().numpy(), y0) < 1e-6
+    assert len(cache.read_text().splitlines()) == 1
+    # malformed lines, then a new key (another batch): searched and appended
+    with open(cache, "a") as f:
+        f.write("not json at all\n{\"key\": \"order=24 batch=4\n")
+    with binding.Plan(n, 4, "r32") as r:
+        r.autotune(x[: 4 * n ** 3], out[: 4 * n ** 3], reps=2)
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 4 and "order=24 batch=4 dtype=" in json.loads(lines[-1])["key"], lines
+
+
 @pytest.mark.parametrize("case", ["r32_n128", "bf16_n64", "ragged", "ragged_persistent", "inverse", "odd_n", "odd_n_inverse",
                                   "bf16_inverse"])
 def test_launch_count_matches_recorded_launches(case):

@@ -92,6 +92,30 @@ def test_orbits_partition_the_grid(n):
         assert frac > (0.6 if n >= 16 else 0.1)
 
 
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+def test_slot_indices_stay_in_the_grid_at_large_orders(n):
+    """The host-side bounds check of the tables the kernels index with, at the
+    large orders: for every orbit and slot, the reduced image W_g k - n wrap
+    lies in [0, n)^3 (so every gather and scatter address lies inside its
+    volume), and the canonical slots cover each grid point exactly once."""
+    d = _tables(n)
+    reps, cls = d["reps"].astype(np.int64), d["cls"].astype(np.int64)
+    assert reps.min() >= 0 and reps.sum(axis=1).max() <= n
+    p = np.einsum("gij,oj->ogi", d["W"].astype(np.int64), reps)        # (orbits, 24, 3)
+    kap = p - n * d["wrap"][cls].astype(np.int64)
+    assert kap.min() >= 0 and kap.max() < n
+    idx = (kap[..., 0] * n + kap[..., 1]) * n + kap[..., 2]
+    canon = d["canon"][cls] == np.arange(24)[None, :]
+    seen = np.bincount(idx[canon], minlength=n ** 3)
+    assert seen.shape == (n ** 3,) and (seen == 1).all()
+    # the free class's wraps are the ones the free-tile kernels build in at
+    # compile time: -1 in row r of slot g exactly where that row of W_g sums
+    # to a negative number (a negated positive form on the open alcove)
+    fc = d["free_class"]
+    fw = np.where(d["W"].sum(axis=2) < 0, -1, 0)
+    assert (d["wrap"][fc] == fw).all()
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 9, 12])
 def test_emulated_forward_inverse_adjoint_match_oracle(n):
     d = _tables(n)
