@@ -651,6 +651,16 @@ def main():
         fwd()
     torch.cuda.synchronize()
     kern = plan.profile_read()
+    # the mixing's access-pattern ceiling: its launches replayed with no
+    # arithmetic, same chunks, geometry and stream (tensor-core forms)
+    replay_ms = None
+    if args.dtype.startswith("r32_") and batch >= 2:
+        for _ in range(args.steps):
+            plan.mixing_replay(x, y)
+        torch.cuda.synchronize()
+        rec = plan.profile_read()
+        if "mix_replay" in rec:
+            replay_ms = rec["mix_replay"][0] / args.steps
     plan.profile(False)
     plan.set_schedule(streams=kept["streams"])
     # algorithmic bytes per real point of each kernel.  Real plans pair two
@@ -778,7 +788,12 @@ def main():
                          "kernel_own_bytes_per_point": algo_bytes.get(top_name, 12),
                          "kernel_own_achieved": own_gbs, "kernel_own_frac": own_gbs / peak,
                          "l2": {"peak": l2_peak, "unit": "GB/s", "frac": own_gbs / l2_peak,
-                                "kind": "measured copy of an L2-resident buffer (read + write)"}},
+                                "kind": "measured copy of an L2-resident buffer (read + write)"},
+                         "access_pattern": None if replay_ms is None or top_name not in ("mix_tc_fwd",) else {
+                             "replay_ms_per_step": replay_ms, "kernel_ms_per_step": top_ms / args.steps,
+                             "frac": replay_ms / (top_ms / args.steps),
+                             "kind": "the kernel's own gathers and stores replayed with no arithmetic "
+                                     "(fcc_dct_diag_mixing_replay; same chunks, grid and stream)"}},
             "step_roofline": {"achieved": step_gbs, "frac": step_gbs / peak, "bytes_per_point": step_bytes},
             "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
             "kernels": {k: {"launches_per_step": v[1] / args.steps, "ms_per_launch": v[0] / v[1],

@@ -255,6 +255,23 @@ fcc_status fcc_dct_profile_enable(fcc_plan* plan, int enable);
 int fcc_dct_profile_read(fcc_plan* plan, char* names, double* ms, int* launches, int cap);
 
 /*
+ * Measurement aid (no counterpart in the paper): replays the global-memory
+ * accesses of the forward tensor-core orbit mixing -- the gathers of all 24
+ * slots of both volumes of every pair and the stores of the canonical slots,
+ * at the addresses, in the chunks and in the launch geometry (grid, block,
+ * shared memory, so the same blocks per SM) of fcc_dct_forward's mixing
+ * stage -- with no arithmetic, on `stream` alone.  Its time is the ceiling
+ * that the mixing's access pattern puts on the mixing kernel (the launches
+ * appear as "mix_replay" in the per-kernel timing).  in: the forward's input
+ * (real volumes, device, 16-byte aligned); out: a buffer of the forward's
+ * output size that receives meaningless values (not overlapping in).
+ * Uniform real tensor-core plans at the canonical shift with batch >= 2 and
+ * free orbits; FCC_ERR_UNSUPPORTED otherwise, FCC_ERR_INVALID_ARG for null,
+ * misaligned or overlapping buffers.
+ */
+fcc_status fcc_dct_diag_mixing_replay(fcc_plan* plan, const void* in, void* out, void* stream);
+
+/*
  * Inverse transform that allocates nothing (the paper has no counterpart).
  *
  * Some callers cannot allocate device memory at the moment they need the

@@ -25,7 +25,7 @@ EXPORTS = [
     "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
     "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host", "fcc_dct_test_fail_alloc",
     "fcc_dct_test_allocations", "fcc_dct_plan_radix2", "fcc_dct_radix2_stats",
-    "fcc_render_cells",
+    "fcc_render_cells", "fcc_dct_diag_mixing_replay",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -67,7 +67,8 @@ def lib():
         L.fcc_dct_describe_skew.restype = i32
         for f in ("fcc_dct_forward", "fcc_dct_inverse", "fcc_dct_adjoint", "fcc_dct_forward_host",
                   "fcc_dct_inverse_host", "fcc_dct_inverse_static", "fcc_dct_forward_packed",
-                  "fcc_dct_inverse_packed", "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host"):
+                  "fcc_dct_inverse_packed", "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host",
+                  "fcc_dct_diag_mixing_replay"):
             getattr(L, f).argtypes = [vp, vp, vp, vp]
             getattr(L, f).restype = i32
         L.fcc_dct_batch.argtypes = [vp]
@@ -302,6 +303,12 @@ class Plan:
             raise ValueError("input must be a contiguous CUDA tensor")
         if out is None:
             out = self._shape_out(x, out_complex)
+        else:   # the C ABI takes plain pointers: the sizes are checked here
+            rt, ct = self._torch_types()
+            want = ct if out_complex else rt
+            if not out.is_cuda or not out.is_contiguous() or out.dtype != want or out.numel() != self.points:
+                raise ValueError("%s: out must be a contiguous CUDA %s tensor with %d elements"
+                                 % (what, want, self.points))
         st = torch.cuda.current_stream(x.device).cuda_stream
         _check(fn(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                   ctypes.c_void_p(st)), what)
@@ -326,6 +333,15 @@ class Plan:
             raise ValueError("adjoint input must be %s with %d elements" % (ct, self.points))
         return self._call(lib().fcc_dct_adjoint, "fcc_dct_adjoint", g, out, not self.real_input)
 
+    def mixing_replay(self, x, out):
+        """Measurement aid: the forward tensor-core mixing's memory accesses with
+        no arithmetic (fcc_dct_diag_mixing_replay); `out` (the forward's output
+        size) receives meaningless values."""
+        rt, _ = self._torch_types()
+        if not self.real_input or x.dtype != rt or x.numel() != self.points:
+            raise ValueError("replay input must be %s with %d elements (real plans)" % (rt, self.points))
+        return self._call(lib().fcc_dct_diag_mixing_replay, "fcc_dct_diag_mixing_replay", x, out, True)
+
     def forward_packed(self, x, out=None):
         """Hermitian-packed forward of a real plan: n^3 reals per volume
         (fcc_dct_forward_packed; layout in include/fcc_dct.h)."""
@@ -341,9 +357,19 @@ class Plan:
             raise ValueError("packed inverse input must be %s with %d elements (real plans)" % (rt, self.points))
         return self._call(lib().fcc_dct_inverse_packed, "fcc_dct_inverse_packed", pk, out, False)
 
+    def _need_host(self, t, what, complex_):
+        """A host buffer of the plan's size (the C ABI cannot check it)."""
+        rt, ct = self._torch_types()
+        want = ct if complex_ else rt
+        if t.is_cuda or not t.is_contiguous() or t.dtype != want or t.numel() != self.points:
+            raise ValueError("%s: host buffers must be contiguous CPU %s tensors with %d elements"
+                             % (what, want, self.points))
+
     def forward_packed_host(self, x_host, pk_host):
         """forward_packed with host tensors (as forward_host)."""
         import torch
+        self._need_host(x_host, "fcc_dct_forward_packed_host", False)
+        self._need_host(pk_host, "fcc_dct_forward_packed_host", False)
         st = torch.cuda.current_stream().cuda_stream
         _check(lib().fcc_dct_forward_packed_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
                                                  ctypes.c_void_p(pk_host.data_ptr()), ctypes.c_void_p(st)),
@@ -353,6 +379,8 @@ class Plan:
     def inverse_packed_host(self, pk_host, x_host):
         """inverse_packed with host tensors (as forward_host)."""
         import torch
+        self._need_host(pk_host, "fcc_dct_inverse_packed_host", False)
+        self._need_host(x_host, "fcc_dct_inverse_packed_host", False)
         st = torch.cuda.current_stream().cuda_stream
         _check(lib().fcc_dct_inverse_packed_host(self.handle, ctypes.c_void_p(pk_host.data_ptr()),
                                                  ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(st)),
@@ -362,6 +390,8 @@ class Plan:
     def inverse_host(self, y_host, x_host):
         """End-to-end inverse with host tensors (see forward_host)."""
         import torch
+        self._need_host(y_host, "fcc_dct_inverse_host", True)
+        self._need_host(x_host, "fcc_dct_inverse_host", not self.real_input)
         st = torch.cuda.current_stream().cuda_stream
         _check(lib().fcc_dct_inverse_host(self.handle, ctypes.c_void_p(y_host.data_ptr()),
                                           ctypes.c_void_p(x_host.data_ptr()), ctypes.c_void_p(st)),
@@ -372,6 +402,8 @@ class Plan:
         """End-to-end call with host tensors (pinned for async copies); the
         caller synchronises the current stream before reading y_host."""
         import torch
+        self._need_host(x_host, "fcc_dct_forward_host", not self.real_input)
+        self._need_host(y_host, "fcc_dct_forward_host", True)
         st = torch.cuda.current_stream().cuda_stream
         _check(lib().fcc_dct_forward_host(self.handle, ctypes.c_void_p(x_host.data_ptr()),
                                           ctypes.c_void_p(y_host.data_ptr()), ctypes.c_void_p(st)),

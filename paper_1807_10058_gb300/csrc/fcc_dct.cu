@@ -24,6 +24,7 @@
 #include "kernels.cuh"
 #include "mix_tc.cuh"
 #include "mix_tc_inv.cuh"
+#include "mix_replay.cuh"
 #include "ragged.cuh"
 #include "mix_tiled.cuh"
 #include "pair.cuh"
@@ -1924,6 +1925,58 @@ fcc_status fcc_dct_autotune(fcc_plan* p, const void* in, void* out, void* stream
         autotune_cache_write(cache, key, sched, best_t);
     }
     return FCC_OK;
+}
+
+fcc_status fcc_dct_diag_mixing_replay(fcc_plan* p, const void* in, void* out, void* stream) {
+    CallRange range("fcc_dct_diag_mixing_replay");
+    if (!p || !in || !out) return fail(FCC_ERR_INVALID_ARG);
+    if (!p->uniform || !is_tc(p->dtype) || p->skew || p->r2 || !p->pairing || p->batch < 2)
+        return fail(FCC_ERR_UNSUPPORTED);
+    const OrderTables& t = p->tabs.at(p->orders[0]);
+    if (t.free_tiles <= 0 || !t.tc_core_image) return fail(FCC_ERR_UNSUPPORTED);
+    if (!aligned16(in) || !aligned16(out)) return fail(FCC_ERR_INVALID_ARG);
+    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + in_bytes(p, 0);
+    const uintptr_t b0 = (uintptr_t)out, b1 = b0 + out_bytes(p, 0);
+    if (a0 < b1 && b0 < a1) return fail(FCC_ERR_INVALID_ARG);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) { cudaGetLastError(); return fail(FCC_ERR_CUDA); }
+    if (cur != p->device) cudaSetDevice(p->device);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const bool bf16 = is_bf16(p->dtype);
+    const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
+    static DeviceOnce attr;
+    if (!attr.done()) {
+        cudaFuncSetAttribute(mix_replay_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<0>::smem);
+        cudaFuncSetAttribute(mix_replay_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcLayout<1>::smem);
+        attr.mark();
+    }
+    // the forward's chunks of pairs (run_group_fast), each chunk's mixing
+    // launch replayed on the caller's stream
+    const int64_t n3 = (int64_t)t.n * t.n * t.n;
+    const int64_t cp = std::min<int64_t>(chunk_vols(p, t.n), std::max<int64_t>(1, p->scratch_points / n3));
+    const int64_t npairs = p->batch / 2;
+    const TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
+    const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups, (const uint4*)t.tc_core_images, t.tc_off, t.canon_mask};
+    const int ngroups = (t.free_tiles + 3) / 4 + t.tc_nbgroups;
+    const int lim = bf16 ? TcLayout<0>::blocks_per_sm : TcLayout<1>::blocks_per_sm;
+    const int per_sm = p->tc_blocks > 0 ? std::min(p->tc_blocks, lim) : lim;
+    g_prof_plan = p;
+    for (int64_t p0 = 0; p0 < npairs; p0 += cp) {
+        const int64_t np = std::min(cp, npairs - p0);
+        for (int64_t v0 = 0; v0 < np; v0 += 65535) {
+            const int64_t nv = std::min<int64_t>(65535, np - v0);
+            const float* src = (const float*)in + (p0 + v0) * 2 * n3;
+            float* dst = (float*)out + (p0 + v0) * 4 * n3;
+            const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)per_sm * p->num_sms / nv + 1));
+            dim3 grid((unsigned)gx, (unsigned)nv);
+            ProfScope ps("mix_replay", st);
+            if (bf16) mix_replay_pair_kernel<0><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, bnd);
+            else mix_replay_pair_kernel<1><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, bnd);
+        }
+    }
+    g_prof_plan = nullptr;
+    if (cur != p->device) cudaSetDevice(cur);
+    return cudaGetLastError() == cudaSuccess ? FCC_OK : fail(FCC_ERR_CUDA);
 }
 
 fcc_status fcc_dct_forward(fcc_plan* p, const void* in, void* out, void* stream) { return dispatch(p, 0, in, out, stream); }

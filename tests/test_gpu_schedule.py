@@ -123,6 +123,33 @@ def test_autotune_keeps_a_valid_schedule(ragged):
         assert rel(y, y0) < 1e-6
 
 
+@pytest.mark.parametrize("dtype", ["r32_bf16x3", "r32_tf32x3"])
+def test_mixing_replay_runs_in_the_forward_geometry(dtype):
+    """The measurement aid replays the forward mixing's launches (same count,
+    same chunks) on one stream and refuses what it does not serve."""
+    n, batch = 64, 6
+    x = torch.from_numpy(inputs.phantom(n, batch, seed=4).reshape(-1).astype(np.float32)).to(DEV)
+    out = torch.empty(n ** 3 * batch, dtype=torch.complex64, device=DEV)
+    with binding.Plan(n, batch, dtype) as p:
+        p.set_schedule(streams=1, chunk_mb=2)   # one pair per chunk: three mixing launches
+        y0 = p.forward(x).cpu().numpy()
+        p.profile(True)
+        p.forward(x, out=out)
+        torch.cuda.synchronize()
+        fwd = p.profile_read()
+        p.mixing_replay(x, out)
+        torch.cuda.synchronize()
+        rep = p.profile_read()
+        p.profile(False)
+        p.check()
+        assert set(rep) == {"mix_replay"}, rep
+        assert rep["mix_replay"][1] == fwd["mix_tc_fwd"][1] == 3, (rep, fwd)
+        # the plan is untouched: the forward still gives the same values
+        assert rel(p.forward(x).cpu().numpy(), y0) == 0.0
+    with binding.Plan(n, batch, "r32") as q, pytest.raises(binding.FccError):
+        q.mixing_replay(x, out)
+
+
 def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     """FCC_AUTOTUNE_CACHE: the first search appends its result as a JSON line;
     a plan of the same key takes the cached schedule without a search (no new
