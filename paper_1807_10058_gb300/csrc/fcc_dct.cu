@@ -949,11 +949,6 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     const int64_t cv = std::min<int64_t>(chunk_vols(p, t.n), std::max<int64_t>(1, p->scratch_points / n3));
     // inverse / adjoint give each stream a slice of the workspace
     const int ns = which == 0 ? p->nstreams : std::min(p->nstreams, p->scratch_streams);
-    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
-    for (int i = 0; i < ns; ++i)
-        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
-    fcc_status s = FCC_OK;
-    int c = 0;
     // real dtypes: two real volumes per complex transform (see pair_split_kernel)
     const bool pairing = rin && p->pairing && nvol >= 2;
     const int64_t npairs = pairing ? nvol / 2 : 0;
@@ -964,6 +959,21 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     // (the tensor-core kernel takes the boundary tiles itself)
     const bool tc_all = is_tc(p->dtype) && t.tc_core_image;
     const bool split_boundary = which == 0 && npairs > 0 && t.free_tiles > 0 && t.ntiles > t.free_tiles && !tc_all;
+    // one chunk, or one internal stream, and no concurrent boundary launch:
+    // everything on the caller's stream, in order, with no fork / join events
+    // (a small call's cost is mostly the enqueueing; with the boundary tiles
+    // on a stream of their own the dependent chain stays one launch shorter)
+    const int64_t nchunks = (npairs + cp - 1) / cp + (nvol - 2 * npairs + cv - 1) / cv;
+    const bool direct = (ns == 1 || nchunks <= 1) && !split_boundary;
+    if (!direct) {
+        if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+        for (int i = 0; i < ns; ++i)
+            if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    auto stream_of = [&](int c) { return direct ? st : p->streams[c % ns]; };
+    auto slice_of = [&](int c) { return direct ? 0 : c % ns; };
+    fcc_status s = FCC_OK;
+    int c = 0;
     if (split_boundary) {
         if (cudaStreamWaitEvent(p->bnd_stream, p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
         s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, npairs, 1.f, p->bnd_stream, true, 2);
@@ -971,7 +981,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     }
     for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
         const int64_t np = std::min(cp, npairs - p0);
-        cudaStream_t ss = p->streams[c % ns];
+        cudaStream_t ss = stream_of(c);
         if (which == 0) {
             const float* x = in + 2 * p0 * n3;
             float* y = out + 2 * p0 * n3 * 2;
@@ -985,7 +995,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             if (!s && split_boundary && cudaStreamWaitEvent(ss, p->bnd_ev, 0) != cudaSuccess) s = FCC_ERR_CUDA;
             if (!s) s = dft3_split_pairs(t, y, np, ss, fold);
         } else {
-            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            float* ws = (float*)p->scratch + (size_t)slice_of(c) * p->scratch_points * 2;
             const float* y = in + 2 * p0 * n3 * 2;
             float* x = out + 2 * p0 * n3;
             s = merge_dft3_pairs(t, y, ws, np, ss);
@@ -996,14 +1006,14 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
     }
     for (int64_t v0 = 2 * npairs; v0 < nvol && !s; v0 += cv, ++c) {
         const int64_t nv = std::min(cv, nvol - v0);
-        cudaStream_t ss = p->streams[c % ns];
+        cudaStream_t ss = stream_of(c);
         if (which == 0) {
             const float* x = in + v0 * n3 * (rin ? 1 : 2);
             float* y = out + v0 * n3 * 2;
             s = launch_mix_tiled(t, MODE_FWD, rin, false, x, y, nv, 1.f, ss);
             if (!s) s = launch_dft3(t, +1, y, y, nv, ss);
         } else {
-            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            float* ws = (float*)p->scratch + (size_t)slice_of(c) * p->scratch_points * 2;
             const float* y = in + v0 * n3 * 2;
             float* x = out + v0 * n3 * (rin ? 1 : 2);
             s = launch_dft3(t, -1, y, ws, nv, ss);
@@ -1011,6 +1021,7 @@ fcc_status run_group_fast(fcc_plan* p, int which, const OrderTables& t, const fl
             if (!s) s = launch_mix_tiled(t, which == 1 ? MODE_INV : MODE_ADJ, false, rin, ws, x, nv, scale, ss);
         }
     }
+    if (direct) return s;
     for (int i = 0; i < ns; ++i) {
         if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
         if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
@@ -1267,15 +1278,19 @@ fcc_status run_pairs_packed(fcc_plan* p, int which, const OrderTables& t, const 
     const float2* tw = (const float2*)t.tw;
     const bool tc = is_tc(p->dtype);
     const bool tc_all = tc && t.tc_core_image;
-    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
-    for (int i = 0; i < ns; ++i)
-        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    // one chunk, or one internal stream: on the caller's stream, no fork / join
+    const bool direct = ns == 1 || npairs <= cp;
+    if (!direct) {
+        if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+        for (int i = 0; i < ns; ++i)
+            if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
     fcc_status s = FCC_OK;
     int c = 0;
     for (int64_t p0 = 0; p0 < npairs && !s; p0 += cp, ++c) {
         const int64_t np = std::min(cp, npairs - p0);
-        cudaStream_t ss = p->streams[c % ns];
-        float* ws = (float*)p->packed_ws + (size_t)(c % ns) * p->packed_slot * 2;
+        cudaStream_t ss = direct ? st : p->streams[c % ns];
+        float* ws = (float*)p->packed_ws + (size_t)(direct ? 0 : c % ns) * p->packed_slot * 2;
         const float* src = in + 2 * p0 * n3;
         float* dst = out + 2 * p0 * n3;
         if (which == 0) {
@@ -1308,6 +1323,7 @@ fcc_status run_pairs_packed(fcc_plan* p, int which, const OrderTables& t, const 
             else if (!s) s = launch_mix_tiled(t, MODE_INV, false, true, ws, dst, np, scale, ss, true);
         }
     }
+    if (direct) return s;
     for (int i = 0; i < ns; ++i) {
         if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
         if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
