@@ -98,6 +98,13 @@ struct OrderTables {
     // ragged plans: point offsets of this order's volumes (device), when all even
     int64_t* voff = nullptr;
     int nvoff = 0;
+    // ragged plans of real volumes: this order's volumes paired in their order
+    // of appearance, two point offsets per pair (pvoff) and the first of each
+    // pair (pzoff, where the pair's complex transform runs); the last volume of
+    // an odd count stays single (voff[nvoff - 1])
+    int64_t* pvoff = nullptr;
+    int64_t* pzoff = nullptr;
+    int npairs_r = 0;
 };
 
 constexpr int kMaxStreams = 4;
@@ -485,6 +492,13 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype, const int* v = nu
                 OrderTables& t = p->tabs[kv.first];
                 t.nvoff = (int)kv.second.size();
                 if ((s = upload(p, (void**)&t.voff, kv.second.data(), kv.second.size() * sizeof(int64_t)))) break;
+                if (is_real_in(dtype) && t.nvoff >= 2) {
+                    t.npairs_r = t.nvoff / 2;
+                    std::vector<int64_t> first((size_t)t.npairs_r);
+                    for (int q = 0; q < t.npairs_r; ++q) first[q] = kv.second[2 * q];
+                    if ((s = upload(p, (void**)&t.pvoff, kv.second.data(), 2 * (size_t)t.npairs_r * sizeof(int64_t)))) break;
+                    if ((s = upload(p, (void**)&t.pzoff, first.data(), first.size() * sizeof(int64_t)))) break;
+                }
             }
     }
     if (s == FCC_OK) {
@@ -719,12 +733,14 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
             dim3 grid((unsigned)((tile1 - tile0 + kMixWarps - 1) / kMixWarps), (unsigned)nv);
             const int nt = tile1;
             if (pair) {
-                // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes;
+                // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes
+                // (ragged: at the first volume of each pair of voff's two point offsets per pair);
                 // inverse / adjoint: compact complex -> real volumes 2p, 2p+1
-                const float* src = in + v0 * a.n3 * 2;
-                float* dst = out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
+                const float* src = voff ? in : in + v0 * a.n3 * 2;
+                float* dst = voff ? out : out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
                 ProfScope ps(names[mode], st);
-                if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                if (voff && mode != MODE_FWD) return FCC_ERR_UNSUPPORTED;
+                if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core, voff ? voff + 2 * v0 : nullptr);
                 else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
                 else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
                 continue;
@@ -1083,6 +1099,11 @@ bool ragged_fast_ok(const fcc_plan* p, int which) {
     return true;
 }
 
+// Pairs of real volumes the ragged forward transforms together at order t.n.
+int ragged_pairs(const fcc_plan* p, const OrderTables& t) {
+    return is_real_in(p->dtype) && p->pairing && t.pvoff ? t.npairs_r : 0;
+}
+
 fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_t st) {
     const bool rin = is_real_in(p->dtype);
     const int ns = p->nstreams;
@@ -1094,9 +1115,27 @@ fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_
     for (auto it = p->tabs.begin(); it != p->tabs.end() && !s; ++it, ++c) {
         const OrderTables& t = it->second;
         cudaStream_t ss = p->streams[c % ns];
-        s = launch_mix_tiled(t, MODE_FWD, rin, false, in, out, t.nvoff, 1.f, ss, false, 0, t.voff);
-        if (!s) s = fast_fft(t.n, true, +1, (const float2*)out, (float2*)out, t.nvoff, (const float2*)t.tw, 0, ss, t.voff);
-        if (!s) s = fast_fft(t.n, false, +1, (const float2*)out, (float2*)out, t.nvoff, (const float2*)t.tw, 0, ss, t.voff);
+        const float2* tw = (const float2*)t.tw;
+        // real volumes: pairs of this order's volumes as one complex transform
+        // each (Z and Y in the first volume's output, the split writes both)
+        const int np = ragged_pairs(p, t);
+        if (np > 0) {
+            s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, np, 1.f, ss, true, 0, t.pvoff);
+            if (!s) s = fast_fft(t.n, true, +1, (const float2*)out, (float2*)out, np, tw, 0, ss, t.pzoff);
+            if (!s) {
+                ProfScope ps("fft_pencil_pair", ss);
+                if (launch_fast_pencil_pair(t.n, (const float2*)out, (float2*)out, np, tw, 0, ss, false, nullptr,
+                                            t.pvoff) != cudaSuccess)
+                    s = FCC_ERR_CUDA;
+            }
+        }
+        const int single = t.nvoff - 2 * np;   // volumes transformed one by one
+        if (single > 0 && !s) {
+            const int64_t* vo = t.voff + 2 * np;
+            s = launch_mix_tiled(t, MODE_FWD, rin, false, in, out, single, 1.f, ss, false, 0, vo);
+            if (!s) s = fast_fft(t.n, true, +1, (const float2*)out, (float2*)out, single, tw, 0, ss, vo);
+            if (!s) s = fast_fft(t.n, false, +1, (const float2*)out, (float2*)out, single, tw, 0, ss, vo);
+        }
     }
     for (int i = 0; i < ns; ++i) {
         if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
@@ -2023,7 +2062,10 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
         if (p->ragged_mode == 1 && ragged_persistent_ok(p)) return 1;
         for (const auto& kv : p->tabs) {
             const OrderTables& t = kv.second;
-            total += (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0) + 2;
+            const int mixl = (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0);
+            const int np = ragged_pairs(p, t), single = t.nvoff - 2 * np;
+            if (np > 0) total += mixl * (int)grid_rows(np) + 2;
+            if (single > 0) total += mixl * (int)grid_rows(single) + 2;
         }
         return total;
     }

@@ -49,9 +49,9 @@ cudaError_t launch_n(bool slab, int sign, const float2* in, float2* out, int64_t
 
 template <int N>
 cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const float2* tw, int64_t vstride,
-                          cudaStream_t st, bool packed, const float2* pre) {
+                          cudaStream_t st, bool packed, const float2* pre, const int64_t* poff) {
     using L = FastLayout<N>;
-    if (vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
+    if (poff ? packed : vstride < 2 * (int64_t)N * N * N) return cudaErrorInvalidValue;
     // packed: 4-byte stores to a separate output (the complex input is not overwritten in place)
     if (packed && (((uintptr_t)out & 3u) != 0 || (const void*)in == (const void*)out)) return cudaErrorInvalidValue;
     const size_t sm = L::pencil_smem, smp = L::pencil_smem + N * sizeof(float2);
@@ -67,8 +67,8 @@ cudaError_t launch_pair_n(const float2* in, float2* out, int64_t npairs, const f
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (packed && pre) fft_pencil_pair_kernel<N, true, true><<<(unsigned)g, kFastThreads, smp, st>>>(in, out, tw, vstride, pre);
     else if (packed) fft_pencil_pair_kernel<N, true><<<(unsigned)g, kFastThreads, sm, st>>>(in, out, tw, vstride);
-    else if (pre) fft_pencil_pair_kernel<N, false, true><<<(unsigned)g, kFastThreads, smp, st>>>(in, out, tw, vstride, pre);
-    else fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, sm, st>>>(in, out, tw, vstride);
+    else if (pre) fft_pencil_pair_kernel<N, false, true><<<(unsigned)g, kFastThreads, smp, st>>>(in, out, tw, vstride, pre, poff);
+    else fft_pencil_pair_kernel<N><<<(unsigned)g, kFastThreads, sm, st>>>(in, out, tw, vstride, nullptr, poff);
     return cudaGetLastError();
 }
 
@@ -134,9 +134,10 @@ cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64
 }
 
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                    int64_t vstride, cudaStream_t st, bool packed, const float2* pre) {
+                                    int64_t vstride, cudaStream_t st, bool packed, const float2* pre,
+                                    const int64_t* poff) {
     switch (n) {
-#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st, packed, pre);
+#define FCC_CASE(NN) case NN: return launch_pair_n<NN>(in, out, npairs, tw, vstride, st, packed, pre, poff);
         FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
         FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
 #undef FCC_CASE

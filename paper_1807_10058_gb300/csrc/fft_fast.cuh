@@ -520,7 +520,7 @@ struct PairLayout {
 template <int N, bool PACKED = false, bool PRE = false>
 __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__ twg, int64_t vstride,
-                       const float2* __restrict__ preg = nullptr) {
+                       const float2* __restrict__ preg = nullptr, const int64_t* __restrict__ poff = nullptr) {
     using L = FastLayout<N>;
     using P = PairLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW, E = R1 / G;
@@ -550,7 +550,12 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
     const bool act = !idle && c < qlim;
     const int lo = partner ? (N - l) % N : l;
     const int co = partner ? (c - l + N) % N : c;
-    const int64_t base = pr * vstride + (int64_t)lo * N + co;     // own pencil; + k * NN
+    // Y of pair pr and D x1 at y0, D x2 at y1 (ragged batches: a table of two
+    // complex offsets per pair; else consecutive volumes)
+    const int64_t y0 = poff ? poff[2 * pr] : pr * vstride;
+    const int64_t y1 = poff ? poff[2 * pr + 1] : y0 + N3;
+    const int64_t base = y0 + (int64_t)lo * N + co;                // own pencil; + k * NN
+    const int64_t base2 = y1 + (int64_t)lo * N + co;
     const int64_t pbase = pr * 2 * N3 + (int64_t)lo * N + co;      // PACKED: own pencil of volume 2p
     float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     float ur[E][G], ui[E][G];
@@ -613,7 +618,7 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
                 o[pbase + N3 + k * NN] = partner ? dr : di;
             } else if (act) {
                 out[base + k * NN] = make_float2(0.5f * (Ar + B.x), 0.5f * (Ai - B.y));
-                out[base + N3 + k * NN] = make_float2(di, -dr);
+                out[base2 + k * NN] = make_float2(di, -dr);
             }
         }
     }
@@ -752,10 +757,12 @@ cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64
                                      cudaStream_t st, bool packed = false);
 // forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
 // (packed: out receives Hermitian-packed real volumes, pair p at p * 2 n^3 floats;
-// pre: n complex factors the inputs are multiplied by along the slow axis, or null)
+// pre: n complex factors the inputs are multiplied by along the slow axis, or null;
+// poff: ragged pairs, two even complex offsets per pair -- Y and D x1 at the
+// first, D x2 at the second; not with packed)
 cudaError_t launch_fast_pencil_pair(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
                                     int64_t vstride, cudaStream_t st, bool packed = false,
-                                    const float2* pre = nullptr);
+                                    const float2* pre = nullptr, const int64_t* poff = nullptr);
 // forward slab pass (+ sign) with the inputs multiplied by pre[c] along the fastest axis
 cudaError_t launch_fast_slab_pre(int n, const float2* in, float2* out, int64_t nvol, const float2* tw,
                                  const float2* pre, int64_t vstride, cudaStream_t st);

@@ -124,9 +124,12 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* rows = reinterpret_cast<float*>(smem_raw) + warp * (32 * kMixRow);   // this warp's [32][kMixRow]
     if (tile >= ntiles) return;                      // warp-uniform; no block barrier below
-    // unpaired volume offset (values): ragged batches pass a table of point offsets
-    const int64_t base = voff ? voff[vol] : vol * a.n3;
-    const int64_t pb = vol * 2 * a.n3;  // paired: first volume of the pair
+    // unpaired volume offset (values): ragged batches pass a table of point
+    // offsets; paired: the two volumes of the pair (ragged batches: a table of
+    // two point offsets per pair), Z in the first volume's complex region
+    const int64_t base = voff && !PAIR ? voff[vol] : vol * a.n3;
+    const int64_t pb = PAIR && voff ? voff[2 * vol] : vol * 2 * a.n3;
+    const int64_t pb1 = PAIR && voff ? voff[2 * vol + 1] : pb + a.n3;
     const int o0 = a.tile_off[tile];
     const int cnt = a.tile_off[tile + 1] - o0;
     const int M8 = 8 * a.n;
@@ -157,7 +160,7 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
             if (act) {
                 if (PAIR && MODE == MODE_FWD) {
                     vr[g] = __ldg(in + pb + gi);
-                    vi[g] = __ldg(in + pb + a.n3 + gi);
+                    vi[g] = __ldg(in + pb1 + gi);
                 } else if (CIN) {
                     const float2 v = __ldg(reinterpret_cast<const float2*>(in) + base + gi);
                     vr[g] = v.x;
@@ -304,7 +307,7 @@ __device__ __forceinline__ void mix_tiled_body(const float* __restrict__ in, flo
             } else if (PAIR) {
                 const float2 v = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
                 out[pb + gi] = v.x;
-                out[pb + a.n3 + gi] = v.y;
+                out[pb1 + gi] = v.y;
             } else if (COUT) {
                 reinterpret_cast<float2*>(out)[base + gi] = *reinterpret_cast<const float2*>(rows + r * kMixRow + 2 * g);
             } else {
