@@ -387,6 +387,19 @@ def secondary_configs(dev):
         rag["per_volume"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(0), "rel_diff": diff}
         ms, sched = p.autotune(x, y, reps=2)
         rag["autotuned"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "schedule": sched, "launches": p.launches(0)}
+        # the inverse of the same batch: per-order launches over the pairs of
+        # each order's volumes, and one launch set per run (no graph)
+        xr = torch.empty_like(x)
+        p.set_schedule(ragged=0)
+        p.forward(x, out=y)
+        ms = _time(lambda: p.inverse(y, out=xr), 5, 2)
+        rt = (torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x)).item()
+        rag["inverse_grouped"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(1),
+                                  "roundtrip_rel_l2": rt}
+        p.set_schedule(ragged=2)
+        ms = _time(lambda: p.inverse(y, out=xr), 3, 1)
+        rag["inverse_per_volume"] = {"value": tot / (ms * 1e-3) / 1e9, "ms": ms, "launches": p.launches(1)}
+        p.set_schedule(**{k: v for k, v in sched.items() if k in ("chunk_mb", "streams", "ragged")})
     out["ragged_1000"] = rag
     # autograd: 50 gradient-descent steps of ||M . (D x) - b||^2, n = 96, batch 32
     n, b = 96, 32

@@ -105,6 +105,7 @@ struct OrderTables {
     int64_t* pvoff = nullptr;
     int64_t* pzoff = nullptr;
     int npairs_r = 0;
+    int64_t single_off = -1;         // host copy of that last volume's point offset
 };
 
 constexpr int kMaxStreams = 4;
@@ -492,6 +493,7 @@ fcc_plan* make_plan(const std::vector<int>& orders, int dtype, const int* v = nu
                 OrderTables& t = p->tabs[kv.first];
                 t.nvoff = (int)kv.second.size();
                 if ((s = upload(p, (void**)&t.voff, kv.second.data(), kv.second.size() * sizeof(int64_t)))) break;
+                if (is_real_in(dtype) && t.nvoff % 2 == 1) t.single_off = kv.second.back();
                 if (is_real_in(dtype) && t.nvoff >= 2) {
                     t.npairs_r = t.nvoff / 2;
                     std::vector<int64_t> first((size_t)t.npairs_r);
@@ -733,16 +735,16 @@ fcc_status launch_mix_tiled(const OrderTables& t, int mode, bool real_in, bool r
             dim3 grid((unsigned)((tile1 - tile0 + kMixWarps - 1) / kMixWarps), (unsigned)nv);
             const int nt = tile1;
             if (pair) {
-                // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes
-                // (ragged: at the first volume of each pair of voff's two point offsets per pair);
-                // inverse / adjoint: compact complex -> real volumes 2p, 2p+1
-                const float* src = voff ? in : in + v0 * a.n3 * 2;
+                // nvol counts pairs; forward: real x (2 volumes per pair) -> complex Z at even volumes;
+                // inverse / adjoint: compact complex -> real volumes 2p, 2p+1.  Ragged (voff: two
+                // point offsets per pair): the real volumes at the listed offsets, Z at the first
+                const int64_t* po = voff ? voff + 2 * v0 : nullptr;
+                const float* src = voff && mode == MODE_FWD ? in : in + v0 * a.n3 * 2;
                 float* dst = voff ? out : out + v0 * a.n3 * (mode == MODE_FWD ? 4 : 2);
                 ProfScope ps(names[mode], st);
-                if (voff && mode != MODE_FWD) return FCC_ERR_UNSUPPORTED;
-                if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core, voff ? voff + 2 * v0 : nullptr);
-                else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
-                else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core);
+                if (mode == MODE_FWD) mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core, po);
+                else if (mode == MODE_INV) mix_tiled_kernel<MODE_INV, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core, po);
+                else mix_tiled_kernel<MODE_ADJ, false, true, true><<<grid, kMixThreads, sm, st>>>(src, dst, a, nt, tile0, core, po);
                 continue;
             }
             const float* src = in + v0 * a.n3 * ((mode == MODE_FWD && real_in) ? 1 : 2);
@@ -1099,6 +1101,59 @@ bool ragged_fast_ok(const fcc_plan* p, int which) {
     return true;
 }
 
+// Ragged inverse / adjoint of real volumes, per order: the pairs (merge fused
+// into the first pencil pass, reading each pair at its two offsets), the slab
+// pass and the inverse mixing writing both volumes back to their offsets, in
+// chunks of the workspace; an odd leftover volume alone.
+bool ragged_fast_inv_ok(const fcc_plan* p) {
+    if (p->uniform || is_double(p->dtype) || !is_real_in(p->dtype) || !p->pairing) return false;
+    for (const auto& kv : p->tabs)
+        if (!kv.second.voff || !has_fast_fft(kv.first)) return false;
+    return true;
+}
+
+fcc_status run_ragged_fast_inv(fcc_plan* p, int which, const float* in, float* out, cudaStream_t st) {
+    const int ns = std::min(p->nstreams, p->scratch_streams);
+    if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return FCC_ERR_CUDA;
+    for (int i = 0; i < ns; ++i)
+        if (cudaStreamWaitEvent(p->streams[i], p->fork_ev, 0) != cudaSuccess) return FCC_ERR_CUDA;
+    const int mode = which == 1 ? MODE_INV : MODE_ADJ;
+    fcc_status s = FCC_OK;
+    int c = 0;
+    for (auto it = p->tabs.begin(); it != p->tabs.end() && !s; ++it) {
+        const OrderTables& t = it->second;
+        const int64_t n3 = (int64_t)t.n * t.n * t.n;
+        const float2* tw = (const float2*)t.tw;
+        const float scale = which == 1 ? (float)(1.0 / (double)n3) : 1.f;
+        const int64_t cp = std::max<int64_t>(1, p->scratch_points / n3);   // pairs per workspace slice
+        for (int64_t p0 = 0; p0 < t.npairs_r && !s; p0 += cp, ++c) {
+            const int64_t np = std::min<int64_t>(cp, t.npairs_r - p0);
+            cudaStream_t ss = p->streams[c % ns];
+            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            {
+                ProfScope ps("fft_pencil_merge", ss);
+                if (launch_fast_pencil_merge(t.n, (const float2*)in, (float2*)ws, np, tw, ss, false, t.pvoff + 2 * p0) !=
+                    cudaSuccess)
+                    s = FCC_ERR_CUDA;
+            }
+            if (!s) s = fast_fft(t.n, true, -1, (const float2*)ws, (float2*)ws, np, tw, n3, ss);
+            if (!s) s = launch_mix_tiled(t, mode, false, true, ws, out, np, scale, ss, true, 0, t.pvoff + 2 * p0);
+        }
+        if (t.single_off >= 0 && !s) {
+            cudaStream_t ss = p->streams[c % ns];
+            float* ws = (float*)p->scratch + (size_t)(c % ns) * p->scratch_points * 2;
+            ++c;
+            s = launch_dft3(t, -1, in + 2 * t.single_off, ws, 1, ss);
+            if (!s) s = launch_mix_tiled(t, mode, false, true, ws, out + t.single_off, 1, scale, ss);
+        }
+    }
+    for (int i = 0; i < ns; ++i) {
+        if (cudaEventRecord(p->join_ev[i], p->streams[i]) != cudaSuccess) return FCC_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, p->join_ev[i], 0) != cudaSuccess) return FCC_ERR_CUDA;
+    }
+    return s;
+}
+
 // Pairs of real volumes the ragged forward transforms together at order t.n.
 int ragged_pairs(const fcc_plan* p, const OrderTables& t) {
     return is_real_in(p->dtype) && p->pairing && t.pvoff ? t.npairs_r : 0;
@@ -1449,6 +1504,8 @@ fcc_status run(fcc_plan* p, int which, const void* vin, void* vout, cudaStream_t
             return run_ragged_persistent(p, (const float*)vin, (float*)vout, st);
         return run_ragged_fast(p, (const float*)vin, (float*)vout, st);
     }
+    if (sizeof(T) == 4 && which != 0 && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_inv_ok(p))
+        return run_ragged_fast_inv(p, which, (const float*)vin, (float*)vout, st);
     const int64_t rs_in = (which == 0 && is_real_in(p->dtype)) ? 1 : 2;
     const int64_t rs_out = (which != 0 && is_real_in(p->dtype)) ? 1 : 2;
     fcc_status s = FCC_OK;
@@ -2066,6 +2123,16 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
             const int np = ragged_pairs(p, t), single = t.nvoff - 2 * np;
             if (np > 0) total += mixl * (int)grid_rows(np) + 2;
             if (single > 0) total += mixl * (int)grid_rows(single) + 2;
+        }
+        return total;
+    }
+    if (!is_double(p->dtype) && which != 0 && p->ragged_fast && p->ragged_mode != 2 && ragged_fast_inv_ok(p)) {
+        for (const auto& kv : p->tabs) {   // run_ragged_fast_inv
+            const OrderTables& t = kv.second;
+            const int mixl = (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0);
+            const int64_t n3 = (int64_t)t.n * t.n * t.n, cp = std::max<int64_t>(1, p->scratch_points / n3);
+            for (int64_t p0 = 0; p0 < t.npairs_r; p0 += cp) total += 2 + mixl * (int)grid_rows(std::min(cp, t.npairs_r - p0));
+            if (t.single_off >= 0) total += 2 + mixl;
         }
         return total;
     }

@@ -100,9 +100,9 @@ cudaError_t launch_slab_pre_n(const float2* in, float2* out, int64_t nvol, const
 
 template <int N>
 cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const float2* tw, cudaStream_t st,
-                           bool packed) {
+                           bool packed, const int64_t* poff) {
     using L = FastLayout<N>;
-    if (packed && ((uintptr_t)in & 3u) != 0) return cudaErrorInvalidValue;
+    if (packed && (((uintptr_t)in & 3u) != 0 || poff)) return cudaErrorInvalidValue;
     static DeviceOnce attr;
     if (!attr.done()) {
         cudaFuncSetAttribute(fft_pencil_merge_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::pencil_smem);
@@ -115,16 +115,16 @@ cudaError_t launch_merge_n(const float2* in, float2* out, int64_t npairs, const 
     if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
     // in_vstride 2 n^3: complex values per pair of complex volumes, or floats per pair of packed ones
     if (packed) fft_pencil_merge_kernel<N, true><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
-    else fft_pencil_merge_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3);
+    else fft_pencil_merge_kernel<N><<<(unsigned)g, kFastThreads, L::pencil_smem, st>>>(in, out, tw, 2 * n3, n3, poff);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                     cudaStream_t st, bool packed) {
+                                     cudaStream_t st, bool packed, const int64_t* poff) {
     switch (n) {
-#define FCC_CASE(NN) case NN: return launch_merge_n<NN>(in, out, npairs, tw, st, packed);
+#define FCC_CASE(NN) case NN: return launch_merge_n<NN>(in, out, npairs, tw, st, packed, poff);
         FCC_CASE(128) FCC_CASE(96) FCC_CASE(88) FCC_CASE(80) FCC_CASE(72) FCC_CASE(64) FCC_CASE(56)
         FCC_CASE(48) FCC_CASE(40) FCC_CASE(32) FCC_CASE(24) FCC_CASE(16) FCC_CASE(8)
 #undef FCC_CASE

@@ -642,7 +642,7 @@ fft_pencil_pair_kernel(const float2* in, float2* out, const float2* __restrict__
 template <int N, bool PACKED = false>
 __global__ void __launch_bounds__(kFastThreads)
 fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ twg,
-                        int64_t in_vstride, int64_t out_vstride) {
+                        int64_t in_vstride, int64_t out_vstride, const int64_t* __restrict__ poff = nullptr) {
     using L = FastLayout<N>;
     using P = PairLayout<N>;
     constexpr int R1 = L::R1, G = L::G, PPW = L::PPW;
@@ -666,7 +666,9 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
     const bool act = !idle && c < qlim;
     const int lo = partner ? (N - l) % N : l;
     const int co = partner ? (c - l + N) % N : c;
-    const int64_t pin = pr * in_vstride + (int64_t)lo * N + co;     // + k * NN; v2 at + N3
+    // v1 at pin, v2 at pin2 (+ k * NN); ragged pairs: two complex offsets per pair
+    const int64_t pin = (poff ? poff[2 * pr] : pr * in_vstride) + (int64_t)lo * N + co;
+    const int64_t pin2 = (poff ? poff[2 * pr + 1] : pr * in_vstride + N3) + (int64_t)lo * N + co;
     const int64_t pout = pr * out_vstride + (int64_t)lo * N + co;
     float2* ex = exall + warp * L::EXW + cl * L::EXPC;
     const float2* cx = l == 0 ? ex : exall + (partner ? warp - kFastWarps / 2 : warp + kFastWarps / 2) * L::EXW + cl * L::EXPC;
@@ -679,7 +681,7 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
         for (int m = 0; m < R1; ++m) {
             const int64_t o = (int64_t)(j + G * m) * NN;
             p1[m] = act ? inf[pin + o] : 0.f;
-            p2[m] = act ? inf[pin + N3 + o] : 0.f;
+            p2[m] = act ? inf[pin2 + o] : 0.f;
         }
         if (!idle) {
 #pragma unroll
@@ -706,7 +708,7 @@ fft_pencil_merge_kernel(const float2* __restrict__ in, float2* __restrict__ out,
         for (int m = 0; m < R1; ++m) {
             const int64_t o = (int64_t)(j + G * m) * NN;
             const float2 a = act ? in[pin + o] : make_float2(0.f, 0.f);
-            const float2 b = act ? in[pin + N3 + o] : make_float2(0.f, 0.f);
+            const float2 b = act ? in[pin2 + o] : make_float2(0.f, 0.f);
             v1r[m] = a.x;
             v1i[m] = a.y;
             v2r[m] = b.x;
@@ -754,7 +756,7 @@ cudaError_t launch_fast_fft(int n, bool slab, int sign, const float2* in, float2
 // compact results at p * n^3 of out
 // (packed: in holds Hermitian-packed real volumes, pair p at p * 2 n^3 floats)
 cudaError_t launch_fast_pencil_merge(int n, const float2* in, float2* out, int64_t npairs, const float2* tw,
-                                     cudaStream_t st, bool packed = false);
+                                     cudaStream_t st, bool packed = false, const int64_t* poff = nullptr);
 // forward pencil pass + pair split over `npairs` pairs (Y of pair p at p * vstride)
 // (packed: out receives Hermitian-packed real volumes, pair p at p * 2 n^3 floats;
 // pre: n complex factors the inputs are multiplied by along the slow axis, or null;
