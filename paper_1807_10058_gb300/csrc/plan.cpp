@@ -318,6 +318,45 @@ int build_host_plan(int n, HostPlan& P, const int* v, int d) {
     }
     std::sort(items.begin(), items.end(),
               [](const Item& x, const Item& y) { return x.key != y.key ? x.key < y.key : x.local < y.local; });
+    // free class: a box of the tiling that the open alcove cuts (fewer than
+    // kTileMax orbits) gives up its own tile; the orbits of such boxes, in box
+    // order, fill tiles of kTileMax (full boxes stay tiles, so the tile order
+    // stays a walk through neighbouring boxes).  Lanes of the kernels' warps
+    // and rows of the tensor-core blocks then carry orbits instead of idling:
+    // at n = 128 a fifth of the tiles go, at n = 32 over half, for the same
+    // sectors per gathered value.
+    {
+        size_t nfree = 0;
+        while (nfree < items.size() && items[nfree].cls == (uint8_t)P.free_class) ++nfree;
+        std::vector<Item> out;
+        out.reserve(nfree);
+        std::vector<Item> pending;
+        int64_t key = 0;
+        auto emit = [&](std::vector<Item>& v, size_t cnt) {
+            for (size_t t = 0; t < cnt; ++t) {
+                v[t].key = key;
+                v[t].local = (int64_t)t;
+                out.push_back(v[t]);
+            }
+            v.erase(v.begin(), v.begin() + (std::ptrdiff_t)cnt);
+            ++key;
+        };
+        size_t i0 = 0;
+        while (i0 < nfree) {
+            size_t e = i0;
+            while (e < nfree && items[e].key == items[i0].key) ++e;
+            std::vector<Item> box(items.begin() + (std::ptrdiff_t)i0, items.begin() + (std::ptrdiff_t)e);
+            if (box.size() == (size_t)kTileMax) {
+                emit(box, box.size());
+            } else {
+                pending.insert(pending.end(), box.begin(), box.end());
+                while (pending.size() >= (size_t)kTileMax) emit(pending, (size_t)kTileMax);
+            }
+            i0 = e;
+        }
+        if (!pending.empty()) emit(pending, pending.size());
+        std::copy(out.begin(), out.end(), items.begin());   // same orbits, keys 0.. in tile order
+    }
     // boundary classes: consecutive runs of kTileMax orbits become tiles
     {
         size_t i0 = 0;
