@@ -78,9 +78,10 @@ def rank_seed(rank):
 
 
 # the sources of the kernels whose DRAM traffic profiles/kernel_traffic.json
-# records (the mixing, slab and pencil passes and what they include)
-TRAFFIC_KERNEL_SOURCES = ("mix_tc.cuh", "mix_tiled.cuh", "kernels.cuh", "plan.h", "weyl_const.h", "fft_fast.cuh",
-                          "fft_slab128.cuh", "dft_reg.cuh")
+# records (the mixing, slab and pencil passes, what they include, and the plan
+# builder that lays out the tiles the mixing walks)
+TRAFFIC_KERNEL_SOURCES = ("mix_tc.cuh", "mix_tiled.cuh", "kernels.cuh", "plan.h", "plan.cpp", "weyl_const.h",
+                          "fft_fast.cuh", "fft_slab128.cuh", "dft_reg.cuh")
 
 
 def kernel_sources_digest():
