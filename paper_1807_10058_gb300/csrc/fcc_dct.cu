@@ -874,7 +874,7 @@ fcc_status merge_dft3_pairs(const OrderTables& t, const float* y, float* ws, int
 // fold: the phase-free form (pair with dft3_split_pairs(..., fold)): the
 // mixing writes the sums without row phase and 1/24, the DFT passes modulate.
 fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const float* in, float* out, int64_t np,
-                               cudaStream_t st, bool fold = false) {
+                               cudaStream_t st, bool fold = false, const int64_t* poff = nullptr) {
     TiledMixArgs a = make_mix_args(t, MODE_FWD, 1.f);
     const bool bf16 = is_bf16(p->dtype);
     const size_t smem = bf16 ? TcLayout<0>::smem : TcLayout<1>::smem;
@@ -887,13 +887,20 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
                              (int)TcLayout<0>::smem);
         cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TcLayout<1>::smem);
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcLayout<0>::smem);
+        cudaFuncSetAttribute(mix_tc_fwd_pair_kernel<1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcLayout<1>::smem);
         attr.mark();
     }
     if (fold && !(t.tc_core_image_f && t.tc_core_image)) return FCC_ERR_UNSUPPORTED;
+    if (fold && poff) return FCC_ERR_UNSUPPORTED;   // the modulated DFT passes take consecutive pairs
     for (int64_t v0 = 0; v0 < np; v0 += 65535) {
         const int64_t nv = std::min<int64_t>(65535, np - v0);
-        const float* src = in + v0 * a.n3 * 2;
-        float* dst = out + v0 * a.n3 * 4;
+        // ragged pairs (poff: two point offsets per pair): the kernel reads its table
+        const float* src = poff ? in : in + v0 * a.n3 * 2;
+        float* dst = poff ? out : out + v0 * a.n3 * 4;
+        const int64_t* po = poff ? poff + 2 * v0 : nullptr;
         if (t.free_tiles > 0 && t.tc_core_image) {
             const int ngroups = (t.free_tiles + 3) / 4 + t.tc_nbgroups;
             const TcBoundary bnd = {t.tc_bgroups, t.tc_nbgroups,
@@ -904,7 +911,13 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             dim3 grid((unsigned)gx, (unsigned)nv);
             ProfScope ps("mix_tc_fwd", st);
             const uint4* ci = (const uint4*)(fold ? t.tc_core_image_f : t.tc_core_image);
-            if (bf16 && fold)
+            if (po && bf16)   // ragged pairs: the table-reading instantiation (row phase in the epilogue)
+                mix_tc_fwd_pair_kernel<0, true, true><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                                p->d_status, bnd, p->wait_test, po);
+            else if (po)
+                mix_tc_fwd_pair_kernel<1, true, true><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
+                                                                                p->d_status, bnd, p->wait_test, po);
+            else if (bf16 && fold)
                 mix_tc_fwd_pair_kernel<0, false><<<grid, kTcThreads, smem, st>>>(src, dst, a, t.free_tiles, t.tc_reps32, ci,
                                                                                  p->d_status, bnd, p->wait_test);
             else if (bf16)
@@ -921,7 +934,7 @@ fcc_status launch_mix_tc_pairs(const fcc_plan* p, const OrderTables& t, const fl
             dim3 grid((unsigned)((t.ntiles + kMixWarps - 1) / kMixWarps), (unsigned)nv);
             ProfScope ps("mix_tiled_fwd", st);
             mix_tiled_kernel<MODE_FWD, true, false, true><<<grid, kMixThreads, mix_tiled_smem_core(t.n), st>>>(
-                src, dst, a, t.ntiles, 0, 1);
+                src, dst, a, t.ntiles, 0, 1, po);
         }
     }
     return cudaGetLastError() == cudaSuccess ? FCC_OK : FCC_ERR_CUDA;
@@ -1175,7 +1188,9 @@ fcc_status run_ragged_fast(fcc_plan* p, const float* in, float* out, cudaStream_
         // each (Z and Y in the first volume's output, the split writes both)
         const int np = ragged_pairs(p, t);
         if (np > 0) {
-            s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, np, 1.f, ss, true, 0, t.pvoff);
+            // tensor-core dtypes mix on the tensor cores (row phase in the epilogue)
+            if (is_tc(p->dtype)) s = launch_mix_tc_pairs(p, t, in, out, np, ss, false, t.pvoff);
+            else s = launch_mix_tiled(t, MODE_FWD, true, false, in, out, np, 1.f, ss, true, 0, t.pvoff);
             if (!s) s = fast_fft(t.n, true, +1, (const float2*)out, (float2*)out, np, tw, 0, ss, t.pzoff);
             if (!s) {
                 ProfScope ps("fft_pencil_pair", ss);
@@ -2121,7 +2136,7 @@ int fcc_dct_launches(const fcc_plan* p, int which) {
             const OrderTables& t = kv.second;
             const int mixl = (t.free_tiles > 0 ? 1 : 0) + (t.ntiles > t.free_tiles ? 1 : 0);
             const int np = ragged_pairs(p, t), single = t.nvoff - 2 * np;
-            if (np > 0) total += mixl * (int)grid_rows(np) + 2;
+            if (np > 0) total += (is_tc(p->dtype) ? 1 : mixl) * (int)grid_rows(np) + 2;
             if (single > 0) total += mixl * (int)grid_rows(single) + 2;
         }
         return total;

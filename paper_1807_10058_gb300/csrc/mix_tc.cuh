@@ -212,11 +212,11 @@ struct TcBoundary {
 // first factor and the 1/24 are a separable modulation of Z that the DFT
 // passes apply to their inputs (fft_slab_kernel / fft_pencil_pair_kernel with
 // PRE), so the kernel writes sum_h w_8^{m_g . v} E[g][h] x[kappa_h] as is.
-template <int KIND, bool PH = true>
+template <int KIND, bool PH = true, bool RG = false>
 __global__ void __launch_bounds__(kTcThreads, TcLayout<KIND>::blocks_per_sm)
 mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, const TiledMixArgs a, int nfree_tiles,
                        const uint32_t* __restrict__ reps32, const uint4* __restrict__ core_image, int* status,
-                       const TcBoundary bnd, int wait_test) {
+                       const TcBoundary bnd, int wait_test, const int64_t* __restrict__ poff = nullptr) {
     using L = TcLayout<KIND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* Cs = smem_raw;                 // core, 96 x 48
@@ -227,7 +227,9 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & 127, half = tid >> 7, wq = warp & 3;   // orbit row; slot half; TMEM lane quarter
     const int n = a.n, M8 = 8 * n;
-    const int64_t pb = (int64_t)blockIdx.y * 2 * a.n3;
+    // pair blockIdx.y: volumes 2p, 2p + 1 (RG, ragged batches: poff's two
+    // point offsets of the pair); Z goes to the first volume's complex region
+    const int64_t pb = RG ? __ldg(poff + 2 * blockIdx.y) : (int64_t)blockIdx.y * 2 * a.n3;
 
     for (int e = tid; e < (int)(L::core_bytes / 16); e += kTcThreads)
         reinterpret_cast<uint4*>(Cs)[e] = core_image[e];
@@ -252,7 +254,7 @@ mix_tc_fwd_pair_kernel(const float* __restrict__ in, float* __restrict__ out, co
     // gather of one tile into registers: two threads per orbit, 24 loads each in flight
     const uint32_t kNone = 0xffffffffu;
     const float* __restrict__ in0 = in + pb;
-    const float* __restrict__ in1 = in + pb + a.n3;
+    const float* __restrict__ in1 = RG ? in + __ldg(poff + 2 * blockIdx.y + 1) : in + pb + a.n3;
     const int nall = ngroups + bnd.ngroups;
     // class of group g (block-uniform; free class for the free groups)
     auto cls_of = [&](int g) -> int { return g < ngroups || g >= nall ? a.free_class : __ldg(bnd.group + 8 * (g - ngroups)); };

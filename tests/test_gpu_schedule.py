@@ -75,6 +75,17 @@ def test_ragged_pairs_of_scattered_volumes(dtype):
         p.profile(False)
         assert sum(c for _, c in rec.values()) == p.launches(0), (rec, p.launches(0))
         assert "fft_pencil_pair" in rec, rec
+        # the same launches captured in a CUDA graph and replayed
+        yg = torch.empty_like(y)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            p.forward(x, out=yg)
+        torch.cuda.current_stream().wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(yg, y)
         y = y.cpu().numpy()
         p.set_schedule(ragged=2)
         y_run = p.forward(x).cpu().numpy()
