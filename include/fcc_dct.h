@@ -435,6 +435,17 @@ fcc_status fcc_dct_describe_skew(int order, const int* v, int d, int* invertible
                                  int* n_classes, int* free_class, uint32_t* reps, int32_t* cls, int32_t* wrap,
                                  int32_t* canon, double* fwd, double* inv, double* adj);
 
+/*
+ * Host-only description of the tiles the orbit-mixing kernels walk at order n
+ * (no CUDA calls).  Fills, when the pointers are non-NULL: ntiles;
+ * free_tiles (the free-class tiles come first); tile_off[ntiles + 1], the
+ * offsets of the tiles in tile_reps; tile_reps[n_orbits], the packed
+ * representatives (as in fcc_dct_describe) in tile order.  A tile holds at
+ * most 32 orbits of one class.  Call once with NULL arrays to learn ntiles.
+ */
+fcc_status fcc_dct_describe_tiles(int order, int32_t* ntiles, int32_t* free_tiles, int32_t* tile_off,
+                                  uint32_t* tile_reps);
+
 /* The 24 group matrices (row-major 3x3 each) the library uses. */
 fcc_status fcc_dct_weyl_group(int32_t* out /* 216 */);
 

@@ -25,7 +25,7 @@ EXPORTS = [
     "fcc_dct_plan_skew", "fcc_dct_describe_skew", "fcc_dct_forward_packed", "fcc_dct_inverse_packed",
     "fcc_dct_forward_packed_host", "fcc_dct_inverse_packed_host", "fcc_dct_test_fail_alloc",
     "fcc_dct_test_allocations", "fcc_dct_plan_radix2", "fcc_dct_radix2_stats",
-    "fcc_render_cells", "fcc_dct_diag_mixing_replay",
+    "fcc_render_cells", "fcc_dct_diag_mixing_replay", "fcc_dct_describe_tiles",
 ]
 
 # execution-schedule keys (fcc_sched_key)
@@ -89,6 +89,8 @@ def lib():
         L.fcc_dct_describe.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                        vp, vp, vp, vp, vp, vp, vp]
         L.fcc_dct_describe.restype = i32
+        L.fcc_dct_describe_tiles.argtypes = [i32, vp, vp, vp, vp]
+        L.fcc_dct_describe_tiles.restype = i32
         L.fcc_dct_weyl_group.argtypes = [vp]
         L.fcc_dct_weyl_group.restype = i32
         L.fcc_dct_profile_enable.argtypes = [vp, i32]
@@ -148,6 +150,21 @@ def describe(order, skew=None):
     return {"reps": k, "cls": cls, "free_class": fc.value, "wrap": wrap.reshape(-1, 24, 3),
             "canon": canon.reshape(-1, 24), "fwd": cx[0], "inv": cx[1], "adj": cx[2],
             "invertible": bool(inv_ok.value)}
+
+
+def describe_tiles(order):
+    """Host-side tile layout of the mixing kernels at the canonical shift (no
+    GPU needed): (tile offsets, free-class tile count, representatives (k1, k2,
+    k3) in tile order)."""
+    L = lib()
+    nt, nf = ctypes.c_int32(), ctypes.c_int32()
+    _check(L.fcc_dct_describe_tiles(order, ctypes.byref(nt), ctypes.byref(nf), None, None), "describe_tiles")
+    off = np.zeros(nt.value + 1, dtype=np.int32)
+    _check(L.fcc_dct_describe_tiles(order, None, None, off.ctypes.data_as(ctypes.c_void_p), None), "describe_tiles")
+    reps = np.zeros(int(off[-1]), dtype=np.uint32)
+    _check(L.fcc_dct_describe_tiles(order, None, None, None, reps.ctypes.data_as(ctypes.c_void_p)), "describe_tiles")
+    k = np.stack([reps & 1023, (reps >> 10) & 1023, (reps >> 20) & 1023], 1).astype(np.int64)
+    return off, nf.value, k
 
 
 def allocations():

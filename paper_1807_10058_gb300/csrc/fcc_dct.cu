@@ -2257,6 +2257,23 @@ fcc_status fcc_dct_describe(int order, int64_t* n_orbits, int* n_classes, int* f
                                  inv, adj);
 }
 
+fcc_status fcc_dct_describe_tiles(int order, int32_t* ntiles, int32_t* free_tiles, int32_t* tile_off,
+                                  uint32_t* tile_reps) {
+    static const int v0[3] = {1, 0, 3};
+    HostPlan hp;
+    const int rc = build_host_plan(order, hp, v0, 8);
+    if (rc == -1) return fail(FCC_ERR_INVALID_ARG);
+    if (rc != 0) return fail(FCC_ERR_UNSUPPORTED);
+    const int nt = (int)hp.tile_off.size() - 1;
+    if (ntiles) *ntiles = nt;
+    if (free_tiles) *free_tiles = hp.free_tiles;
+    if (tile_off)
+        for (int t = 0; t <= nt; ++t) tile_off[t] = hp.tile_off[t];
+    if (tile_reps)
+        for (size_t o = 0; o < hp.tile_reps.size(); ++o) tile_reps[o] = hp.tile_reps[o];
+    return FCC_OK;
+}
+
 fcc_status fcc_dct_describe_skew(int order, const int* v, int d, int* invertible, int64_t* n_orbits, int* n_classes,
                                  int* free_class, uint32_t* reps, int32_t* cls, int32_t* wrap, int32_t* canon,
                                  double* fwd, double* inv, double* adj) {

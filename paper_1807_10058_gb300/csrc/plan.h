@@ -78,10 +78,12 @@ struct HostPlan {
     // Tiles for the locality-aware mixing kernel.  With
     //   a' = k1 + k2 + k3, b' = k1 + k2, c' = k1
     // the representative is k = a' e3 + b' (0,1,-1) + c' (1,-1,0) and the
-    // closed alcove is n >= a' >= b' >= c' >= 0.  Representatives are grouped
-    // into boxes of kTileA x kTileB x kTileC in (a', b', c'); within a tile
-    // they are listed with a' fastest (then b', then c').  perm_b / perm_c list
-    // the same tile with b' (resp. c') fastest, as indices into that order.
+    // closed alcove is n >= a' >= b' >= c' >= 0.  Free representatives are
+    // grouped into boxes of kTileA x kTileB x kTileC in (a', b', c'): a full
+    // box is a tile (a' fastest, then b', then c'); the orbits of boxes the
+    // alcove cuts fill tiles of kTileMax in box order.  Boundary classes come
+    // after, in runs of kTileMax per class.  perm_b / perm_c list each tile
+    // with b' (resp. c') fastest, as indices into its order.
     std::vector<int32_t> tile_off;   // [ntiles + 1], offsets into tile_reps
     std::vector<uint32_t> tile_reps; // packed representatives, tile order
     std::vector<uint8_t> tile_cls;

@@ -92,6 +92,48 @@ def test_orbits_partition_the_grid(n):
         assert frac > (0.6 if n >= 16 else 0.1)
 
 
+@pytest.mark.parametrize("n", [8, 16, 24, 32, 64, 128])
+def test_tiles_partition_the_orbits(n):
+    """The tiles the mixing kernels walk: at most 32 orbits of one class each,
+    every orbit in exactly one tile, the free class first; each free tile is a
+    whole 4 x 4 x 2 box of (a', b', c') = (k1+k2+k3, k1+k2, k1) or a full run
+    of 32 orbits of cut boxes (the last one may be short), and no free tile
+    could be merged with another: at most one short free tile, and the box
+    tiles are exactly the boxes the alcove leaves whole."""
+    d = binding.describe(n)
+    off, nfree, tk = binding.describe_tiles(n)
+    sizes = np.diff(off)
+    assert off[0] == 0 and (sizes >= 1).all() and (sizes <= 32).all()
+    key = lambda k: tuple(k.tolist())
+    order_cls = {key(k): c for k, c in zip(d["reps"], d["cls"])}
+    assert sorted(map(key, tk)) == sorted(map(key, d["reps"]))          # a partition of the orbits
+    tcls = np.array([order_cls[key(k)] for k in tk])
+    for t in range(len(sizes)):
+        c = tcls[off[t]:off[t + 1]]
+        assert (c == c[0]).all(), t                                     # class-pure
+        assert (t < nfree) == (c[0] == d["free_class"]), t               # free tiles first
+    if nfree == 0:
+        return
+    free = d["reps"][d["cls"] == d["free_class"]]
+    box_of = lambda k: ((k[:, 0] + k[:, 1] + k[:, 2]) // 4, (k[:, 0] + k[:, 1]) // 4, k[:, 0] // 2)
+    ba, bb, bc = box_of(free)
+    _, counts = np.unique(np.stack([ba, bb, bc], 1), axis=0, return_counts=True)
+    whole = (counts == 32).sum()
+    short = 0
+    box_tiles = 0
+    for t in range(nfree):
+        k = tk[off[t]:off[t + 1]]
+        a, b, c = box_of(k)
+        one_box = len(set(zip(a.tolist(), b.tolist(), c.tolist()))) == 1
+        if len(k) == 32 and one_box:
+            box_tiles += 1
+        short += len(k) < 32
+    assert short <= 1
+    assert box_tiles == whole   # a merged tile of 32 cannot come from one cut box
+    cut = len(free) - 32 * whole
+    assert nfree == whole + (cut + 31) // 32, (nfree, whole, cut)
+
+
 @pytest.mark.parametrize("n", [32, 64, 96, 128])
 def test_slot_indices_stay_in_the_grid_at_large_orders(n):
     """The host-side bounds check of the tables the kernels index with, at the
