@@ -818,7 +818,10 @@ def main():
             "kernel_timing": "CUDA events around each launch, one internal stream (each kernel alone)",
             "e2e": {"value": world * pts / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
-                    "pinned_copy_gbs": link},
+                    "pinned_copy_gbs": link,
+                    # the slower direction alone, at its measured one-way rate
+                    "link_bound_ms": max(xh.numel() * 4 / (link["h2d_gbs"] * 1e9),
+                                         yh.numel() * yh.element_size() / (link["d2h_gbs"] * 1e9)) * 1e3},
             "gpu_launches": plan.launches(3 if packed else 0) * args.steps,
             "clocks": ck,
             "accuracy": accuracy,
